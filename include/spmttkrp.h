@@ -1,0 +1,210 @@
+/*
+ * spmttkrp.h - C ABI of the GB300 all-mode sparse MTTKRP engine.
+ *
+ * Method: Wijeratne, Kannan, Prasanna, "Sparse MTTKRP Acceleration for Tensor
+ * Decomposition on GPU" (CF '24).  A COO tensor X with N modes is kept on the
+ * device as ONE working copy of its nonzeros.  Computing the mode-n MTTKRP
+ *     M_n = X_(n) (Khatri-Rao product of the A_k, k != n)          (Eq. 1)
+ * streams that copy, gathers the factor rows A_k[i_k, :], and at the same
+ * time scatters every nonzero to its place in the next mode's order (the
+ * dynamic tensor remap, Section 3.1, Algorithm 3), so that mode n+1 again
+ * reads a copy sorted by its own output index (Algorithm 5).  The nonzeros of
+ * one mode are cut into blocks that own disjoint output rows, so no global
+ * atomics are used (Observation 2); rows heavier than a block are split and
+ * summed afterwards in block order.  Every output row is written once.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an int status (SPM_OK or a negative SPM_ERR_*) and
+ *     never aborts; spmttkrp_last_error() gives a thread-local message.
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device, owned by the caller, unless stated otherwise.  "host" pointers
+ *     are ordinary CPU memory owned by the caller.
+ *   - Work is queued asynchronously on the plan's stream (opts.stream, or
+ *     spmttkrp_set_stream); only calls documented as synchronizing wait.
+ *   - Indices are 0-based; every dims[k] must be in [1, 2^31-1]; nnz < 2^31;
+ *     2 <= nmodes <= 16; 1 <= rank <= 256.
+ *   - Factor matrices are dense, row-major I_k x R, with row stride R
+ *     elements; FP32, or BF16 when the plan was made with SPM_DTYPE_BF16.
+ *     Outputs and gradients are FP32, row-major I_n x R.
+ */
+#ifndef SPMTTKRP_H
+#define SPMTTKRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spmttkrp_plan* spmttkrp_plan_t;
+
+enum spm_status {
+  SPM_OK = 0,
+  SPM_ERR_INVALID_ARG = -1, /* null pointer, bad mode, bad size or option        */
+  SPM_ERR_INDEX_RANGE = -2, /* a coordinate outside [0, dims[k])                   */
+  SPM_ERR_DUPLICATE = -3,   /* two nonzeros share a coordinate                      */
+  SPM_ERR_OOM = -4,         /* host or device allocation failed, or max_bytes hit  */
+  SPM_ERR_CUDA = -5,        /* a CUDA runtime call failed                           */
+  SPM_ERR_UNSUPPORTED = -6, /* sizes beyond the limits above                        */
+  SPM_ERR_NOT_SPD = -7,     /* ALS: the Hadamard of Gram matrices is not SPD        */
+  SPM_ERR_STATE = -8,       /* call not valid for this plan (host-only, destroyed) */
+  SPM_ERR_TIMEOUT = -9      /* a bounded device wait gave up (no hang, no trap)     */
+};
+
+enum spm_dtype { SPM_DTYPE_F32 = 0, SPM_DTYPE_BF16 = 1 };
+
+typedef struct {
+  int factor_dtype; /* SPM_DTYPE_F32 or SPM_DTYPE_BF16 (factor storage only)     */
+  int partition;    /* 0 = contiguous split with heavy-row splitting (only one)  */
+  int nblk;         /* blocks per mode; 0 = size-based default                    */
+  int tile;         /* nonzeros staged per shared-memory tile: 0 (=512), 256, 512,
+                       1024                                                        */
+  size_t max_bytes; /* cap on the plan's device memory; 0 = no cap               */
+  int checks;       /* 1 = synchronize and read the device error word after every
+                       compute call (slow; for debugging)                         */
+  int host_only;    /* 1 = build the plan on the host only (no device memory);
+                       only spmttkrp_plan_query and destroy are then valid        */
+  void* stream;     /* cudaStream_t for all work; NULL = default stream           */
+} spmttkrp_opts_t;
+
+/* Fills *opts with the defaults (FP32, contiguous split, automatic sizes). */
+int spmttkrp_opts_init(spmttkrp_opts_t* opts);
+
+/*
+ * Builds a plan (the paper's preprocessing, Section 3.4 / 3.5 and the
+ * evaluation's preprocessing step): validates the COO, sorts the nonzeros
+ * into every mode's canonical order K_n = (i_n, i_{n-1}, ..., i_{n+1})
+ * (lexicographic), computes the remap ids next_pos_n (position in the
+ * mode-(n+1) order of the nonzero at position p of the mode-n order), the
+ * block boundaries of every mode and the split-row tables, and uploads the
+ * working copy (mode-0 order) and these tables to the device.
+ *   out    host, receives the plan handle (owned by the caller; destroy it).
+ *   coo    host, int64 [nnz][nmodes] row-major coordinates, any order.
+ *   vals   host, float [nnz] values.
+ *   nnz    number of nonzeros (0 allowed: every output is then all zeros).
+ *   dims   host, int64 [nmodes].
+ *   rank   R of the factor matrices the plan will be used with.
+ *   opts   host, nullable (defaults).
+ * Errors: INVALID_ARG, INDEX_RANGE, DUPLICATE, UNSUPPORTED, OOM, CUDA.
+ * Synchronizes the plan's stream before returning.
+ */
+int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* vals,
+                         int64_t nnz, const int64_t* dims, int nmodes, int rank,
+                         const spmttkrp_opts_t* opts);
+
+/* Frees the plan and every device buffer it owns (synchronizes its stream). */
+int spmttkrp_plan_destroy(spmttkrp_plan_t plan);
+
+/* Sets the stream (cudaStream_t) later calls queue their work on. */
+int spmttkrp_set_stream(spmttkrp_plan_t plan, void* stream);
+
+/*
+ * Dynamic tensor remap only (Section 3.1, Algorithm 3): brings the working
+ * copy into the given mode's canonical order by pure remap passes (no-op when
+ * it is already there).  Errors: INVALID_ARG (mode), STATE.
+ */
+int spmttkrp_remap(spmttkrp_plan_t plan, int mode);
+
+/*
+ * Mode-n spMTTKRP (Eq. 1; Algorithms 2, 4) fused with the remap of the
+ * working copy into mode (n+1) mod N order (Algorithm 3).  Remaps first if the
+ * copy is not in mode-n order.
+ *   factors  host array of nmodes device pointers (the mode-n one is not read).
+ *   out      device, float [dims[mode]][rank], fully overwritten (rows with no
+ *            nonzero are written as zeros); must not alias a factor.
+ * Errors: INVALID_ARG, STATE, CUDA, TIMEOUT (with opts.checks).
+ */
+int spmttkrp_compute(spmttkrp_plan_t plan, int mode, const void* const* factors, float* out);
+
+/* flags for spmttkrp_sweep */
+enum { SPM_SWEEP_GRAPH = 1 /* replay the sweep as one captured CUDA graph */ };
+
+/*
+ * All-mode spMTTKRP (Algorithm 5): M_n for every mode n with the same input
+ * factors, one fused compute+remap pass per mode, starting from the mode the
+ * working copy is in; afterwards the copy is back in that mode's order.
+ *   factors  host array of nmodes device pointers.
+ *   outs     host array of nmodes device pointers, float [dims[n]][rank].
+ *   flags    0 or SPM_SWEEP_GRAPH.
+ */
+int spmttkrp_sweep(spmttkrp_plan_t plan, const void* const* factors, float* const* outs,
+                   int flags);
+
+/*
+ * One CP-ALS iteration over modes 0..N-1 (Section 2.1.3; Kolda-Bader update):
+ * per mode M_n = spMTTKRP, V = Hadamard of the Gram matrices A_k^T A_k (k != n)
+ * in FP64, Cholesky of V in FP64, A_n = M_n V^-1, lambda = column 2-norms of
+ * A_n, A_n /= lambda.  Replayed from a captured CUDA graph after the first
+ * call with the same pointers.
+ *   factors  host array of nmodes device pointers, read and overwritten.
+ *   lambda   device, float [rank], written.
+ *   fit      host, receives 1 - |X - Y|_F / |X|_F; this call synchronizes.
+ * Errors: NOT_SPD (factors unchanged from the failing mode on), INVALID_ARG,
+ * STATE, CUDA.
+ */
+int cp_als_iter(spmttkrp_plan_t plan, void* const* factors, float* lambda, double* fit);
+
+/*
+ * CP loss on the observed entries: L = 1/2 sum_e (m_e - x_e)^2 with
+ * m_e = sum_r prod_k A_k[i_k(e), r]; keeps the residuals m_e - x_e in the plan.
+ *   factors  host array of nmodes device pointers.
+ *   loss     device, float scalar, written.
+ */
+int cp_loss_fwd(spmttkrp_plan_t plan, const void* const* factors, float* loss);
+
+/*
+ * Gradient of the CP loss: grads[n] = grad_out * spMTTKRP_n(residual tensor)
+ * for every mode, one all-mode sweep on a remapped copy of the residuals.
+ * Needs a previous cp_loss_fwd with the same factors.
+ *   grad_out device, float scalar (dL_total/dL).
+ *   grads    host array of nmodes device pointers, float [dims[n]][rank].
+ */
+int cp_loss_bwd(spmttkrp_plan_t plan, const void* const* factors, const float* grad_out,
+                float* const* grads);
+
+/*
+ * Chooses blocks per mode and tile size by timing all-mode sweeps with CUDA
+ * events on the plan's own data, and applies the winner (deterministic
+ * argmin of the median, ties to the first candidate).  Results are cached in
+ * the JSON file named by $SPMTTKRP_TUNE_CACHE when set.
+ *   factors  host array of nmodes device pointers used for the trial sweeps.
+ *   scratch  host array of nmodes device output buffers for the trial sweeps.
+ *   flags    bit 0: ignore the cache.
+ */
+int spmttkrp_autotune(spmttkrp_plan_t plan, const void* const* factors, float* const* scratch,
+                      int flags);
+
+/* what for spmttkrp_plan_query */
+enum {
+  SPM_Q_INFO = 0,     /* int64[16]: nnz, nmodes, rank, elem_bytes, cur_mode, dtype,
+                         tile, nblk(mode), nsplit(mode), launches per sweep,
+                         device bytes, ...                                          */
+  SPM_Q_NEXT_POS = 1, /* int32[nnz]: next_pos of `mode`                            */
+  SPM_Q_BOUNDS = 2,   /* int64[nblk+1]: block boundaries of `mode`                 */
+  SPM_Q_SPLITS = 3,   /* int64[nsplit][3]: (row, first_blk, last_blk) of `mode`   */
+  SPM_Q_ELEMS = 4,    /* int32[nnz][nmodes] indices of the working copy, in its
+                         current order                                             */
+  SPM_Q_VALS = 5      /* float[nnz] values of the working copy, same order         */
+};
+
+/* Copies plan data into host memory (synchronizes).  bytes must be >= the
+ * size stated above for `what`.  Errors: INVALID_ARG, STATE, CUDA. */
+int spmttkrp_plan_query(spmttkrp_plan_t plan, int what, int mode, void* host_dst,
+                        size_t bytes);
+
+/* Synchronizes, returns SPM_OK or the first recorded device-side error
+ * (e.g. SPM_ERR_TIMEOUT) and clears it. */
+int spmttkrp_device_status(spmttkrp_plan_t plan);
+
+/* Thread-local text for the last non-OK status of this thread. */
+const char* spmttkrp_last_error(void);
+
+/* ABI version (major * 100 + minor). */
+int spmttkrp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMTTKRP_H */

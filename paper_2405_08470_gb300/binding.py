@@ -1,0 +1,230 @@
+"""Thin ctypes binding of the engine's C ABI (``include/spmttkrp.h``).
+
+Argument marshalling only: every step of the computation runs inside the
+CUDA library.  Tensors are passed as raw pointers (``data_ptr()``), streams as
+``torch.cuda.current_stream().cuda_stream``.  Importing this module never
+falls back to anything: if the shared library is missing or fails to load,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+SPM_OK = 0
+STATUS = {
+    0: "SPM_OK", -1: "SPM_ERR_INVALID_ARG", -2: "SPM_ERR_INDEX_RANGE", -3: "SPM_ERR_DUPLICATE",
+    -4: "SPM_ERR_OOM", -5: "SPM_ERR_CUDA", -6: "SPM_ERR_UNSUPPORTED", -7: "SPM_ERR_NOT_SPD",
+    -8: "SPM_ERR_STATE", -9: "SPM_ERR_TIMEOUT",
+}
+DTYPES = {"f32": 0, "bf16": 1}
+Q_INFO, Q_NEXT_POS, Q_BOUNDS, Q_SPLITS, Q_ELEMS, Q_VALS = range(6)
+SWEEP_GRAPH = 1
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                      "include", "spmttkrp.h")
+
+
+class SpmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("factor_dtype", ctypes.c_int), ("partition", ctypes.c_int),
+                ("nblk", ctypes.c_int), ("tile", ctypes.c_int),
+                ("max_bytes", ctypes.c_size_t), ("checks", ctypes.c_int),
+                ("host_only", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+_LIB = None
+P = ctypes.c_void_p
+I64P = ctypes.POINTER(ctypes.c_int64)
+
+
+def declared_functions():
+    """Names of the functions ``include/spmttkrp.h`` declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(\w+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    """Loads the engine library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"engine library missing ({_build.LIB}); run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    L.spmttkrp_version.restype = ctypes.c_int
+    L.spmttkrp_last_error.restype = ctypes.c_char_p
+    L.spmttkrp_opts_init.argtypes = [ctypes.POINTER(Opts)]
+    L.spmttkrp_plan_create.argtypes = [ctypes.POINTER(P), P, P, ctypes.c_int64, I64P,
+                                       ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts)]
+    L.spmttkrp_plan_destroy.argtypes = [P]
+    L.spmttkrp_set_stream.argtypes = [P, P]
+    L.spmttkrp_remap.argtypes = [P, ctypes.c_int]
+    L.spmttkrp_compute.argtypes = [P, ctypes.c_int, P, P]
+    L.spmttkrp_sweep.argtypes = [P, P, P, ctypes.c_int]
+    L.cp_als_iter.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double)]
+    L.cp_loss_fwd.argtypes = [P, P, P]
+    L.cp_loss_bwd.argtypes = [P, P, P, P]
+    L.spmttkrp_autotune.argtypes = [P, P, P, ctypes.c_int]
+    L.spmttkrp_plan_query.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t]
+    L.spmttkrp_device_status.argtypes = [P]
+    for name in declared_functions():
+        getattr(L, name).restype = ctypes.c_char_p if name == "spmttkrp_last_error" \
+            else ctypes.c_int
+    _LIB = L
+    return L
+
+
+def check(status: int):
+    if status != SPM_OK:
+        raise SpmError(status, lib().spmttkrp_last_error().decode(errors="replace"))
+
+
+def _ptrs(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = None if t is None else ctypes.c_void_p(t.data_ptr())
+    return arr
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream) if hasattr(stream, "cuda_stream") \
+        else ctypes.c_void_p(stream)
+
+
+class Plan:
+    """One COO tensor prepared for all-mode spMTTKRP on the current CUDA device."""
+
+    def __init__(self, coo, vals, dims: Sequence[int], rank: int, dtype: str = "f32",
+                 nblk: int = 0, tile: int = 0, max_bytes: int = 0, checks: bool = False,
+                 host_only: bool = False, stream=None):
+        L = lib()
+        coo = np.ascontiguousarray(np.asarray(coo.cpu() if hasattr(coo, "cpu") else coo,
+                                              dtype=np.int64))
+        vals = np.ascontiguousarray(np.asarray(vals.cpu() if hasattr(vals, "cpu") else vals,
+                                               dtype=np.float32))
+        self.dims = tuple(int(d) for d in dims)
+        self.nmodes = len(self.dims)
+        self.rank = int(rank)
+        self.nnz = int(vals.shape[0])
+        self.dtype = dtype
+        o = Opts()
+        L.spmttkrp_opts_init(ctypes.byref(o))
+        o.factor_dtype = DTYPES[dtype]
+        o.nblk, o.tile, o.max_bytes = int(nblk), int(tile), int(max_bytes)
+        o.checks, o.host_only = int(bool(checks)), int(bool(host_only))
+        o.stream = None if host_only else _stream_ptr(stream)
+        d = np.asarray(self.dims, dtype=np.int64)
+        h = ctypes.c_void_p()
+        st = L.spmttkrp_plan_create(ctypes.byref(h),
+                                    coo.ctypes.data if coo.size else None,
+                                    vals.ctypes.data if vals.size else None,
+                                    self.nnz, d.ctypes.data_as(I64P), self.nmodes, self.rank,
+                                    ctypes.byref(o))
+        check(st)
+        self._h = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            check(lib().spmttkrp_plan_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        check(lib().spmttkrp_set_stream(self._h, _stream_ptr(stream)))
+
+    # -- compute
+    def remap(self, mode: int):
+        check(lib().spmttkrp_remap(self._h, int(mode)))
+
+    def compute(self, mode: int, factors, out):
+        check(lib().spmttkrp_compute(self._h, int(mode), _ptrs(factors),
+                                     ctypes.c_void_p(out.data_ptr())))
+
+    def sweep(self, factors, outs, graph: bool = False):
+        check(lib().spmttkrp_sweep(self._h, _ptrs(factors), _ptrs(outs),
+                                   SWEEP_GRAPH if graph else 0))
+
+    def als_iter(self, factors, lam) -> float:
+        fit = ctypes.c_double()
+        check(lib().cp_als_iter(self._h, _ptrs(factors), ctypes.c_void_p(lam.data_ptr()),
+                                ctypes.byref(fit)))
+        return fit.value
+
+    def loss_fwd(self, factors, loss):
+        check(lib().cp_loss_fwd(self._h, _ptrs(factors), ctypes.c_void_p(loss.data_ptr())))
+
+    def loss_bwd(self, factors, grad_out, grads):
+        check(lib().cp_loss_bwd(self._h, _ptrs(factors), ctypes.c_void_p(grad_out.data_ptr()),
+                                _ptrs(grads)))
+
+    def autotune(self, factors, scratch, ignore_cache: bool = False):
+        check(lib().spmttkrp_autotune(self._h, _ptrs(factors), _ptrs(scratch),
+                                      1 if ignore_cache else 0))
+
+    def device_status(self):
+        check(lib().spmttkrp_device_status(self._h))
+
+    # -- queries
+    def info(self, mode: int = 0) -> dict:
+        buf = np.zeros(16, dtype=np.int64)
+        check(lib().spmttkrp_plan_query(self._h, Q_INFO, int(mode), buf.ctypes.data, buf.nbytes))
+        keys = ["nnz", "nmodes", "rank", "elem_bytes", "cur_mode", "dtype", "tile", "nblk",
+                "nsplit", "launches_per_sweep", "device_bytes", "cur_buf", "host_only",
+                "num_sms", "normx2", "lanes"]
+        d = dict(zip(keys, buf.tolist()))
+        d["normx2"] = float(buf[14:15].view(np.float64)[0])
+        return d
+
+    def next_pos(self, mode: int) -> np.ndarray:
+        out = np.zeros(self.nnz, dtype=np.int32)
+        check(lib().spmttkrp_plan_query(self._h, Q_NEXT_POS, int(mode), out.ctypes.data,
+                                        out.nbytes))
+        return out
+
+    def bounds(self, mode: int) -> np.ndarray:
+        nblk = self.info(mode)["nblk"]
+        out = np.zeros(nblk + 1, dtype=np.int64)
+        check(lib().spmttkrp_plan_query(self._h, Q_BOUNDS, int(mode), out.ctypes.data,
+                                        out.nbytes))
+        return out
+
+    def splits(self, mode: int) -> np.ndarray:
+        ns = self.info(mode)["nsplit"]
+        out = np.zeros((ns, 3), dtype=np.int64)
+        check(lib().spmttkrp_plan_query(self._h, Q_SPLITS, int(mode),
+                                        out.ctypes.data if ns else
+                                        np.zeros(1, np.int64).ctypes.data, max(out.nbytes, 8)))
+        return out
+
+    def elements(self):
+        """Working copy (indices int32 [nnz, N], values float32 [nnz]) in its current order."""
+        idx = np.zeros((self.nnz, self.nmodes), dtype=np.int32)
+        val = np.zeros(self.nnz, dtype=np.float32)
+        if self.nnz:
+            check(lib().spmttkrp_plan_query(self._h, Q_ELEMS, 0, idx.ctypes.data, idx.nbytes))
+            check(lib().spmttkrp_plan_query(self._h, Q_VALS, 0, val.ctypes.data, val.nbytes))
+        return idx, val

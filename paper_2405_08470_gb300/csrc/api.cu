@@ -1,0 +1,512 @@
+// api.cu - the C ABI of the engine: plan lifetime, remap, per-mode compute and
+// the all-mode sweep (Algorithm 5), plus plan queries and error reporting.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "engine.h"
+#include "mttkrp_kernel.cuh"
+
+namespace spm {
+
+static thread_local std::string g_last_error;
+
+int fail(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return SPM_ERR_CUDA;
+}
+
+static int dalloc(spmttkrp_plan* p, void** ptr, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 16);
+  if (p->max_bytes && p->dev_bytes + bytes > p->max_bytes)
+    return fail(SPM_ERR_OOM, "plan device memory cap (max_bytes) exceeded");
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(SPM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  p->dev_bytes += bytes;
+  return SPM_OK;
+}
+
+static void dfree(void* ptr) {
+  if (ptr) cudaFree(ptr);
+}
+
+// Uploads one mode's block descriptors and split table (after (re)partitioning).
+int upload_mode_tables(spmttkrp_plan* p, int n) {
+  ModeHost& h = p->mh[(size_t)n];
+  ModeDev& d = p->md[(size_t)n];
+  if (d.blkinfo) {
+    cudaFree(d.blkinfo);
+    p->dev_bytes -= std::max<size_t>((size_t)d.nblk * sizeof(int4), 16);
+    d.blkinfo = nullptr;
+  }
+  if (d.splits) {
+    cudaFree(d.splits);
+    p->dev_bytes -= std::max<size_t>((size_t)d.nsplit * sizeof(SplitRow), 16);
+    d.splits = nullptr;
+  }
+  d.nblk = h.nblk;
+  d.nsplit = (int)h.splits.size();
+  d.last_row = h.last_row;
+  int st = dalloc(p, (void**)&d.blkinfo, (size_t)d.nblk * sizeof(int4));
+  if (st) return st;
+  st = dalloc(p, (void**)&d.splits, (size_t)d.nsplit * sizeof(SplitRow));
+  if (st) return st;
+  SPM_CUDA(cudaMemcpyAsync(d.blkinfo, h.blkinfo.data(), (size_t)d.nblk * sizeof(int4),
+                           cudaMemcpyHostToDevice, p->stream));
+  if (d.nsplit)
+    SPM_CUDA(cudaMemcpyAsync(d.splits, h.splits.data(), (size_t)d.nsplit * sizeof(SplitRow),
+                             cudaMemcpyHostToDevice, p->stream));
+  // partial-sum buffer: 2 slots of R floats per block
+  size_t need = (size_t)d.nblk * 2 * p->R;
+  if (need > p->part_cap) {
+    if (p->d_part) {
+      cudaFree(p->d_part);
+      p->dev_bytes -= std::max<size_t>(p->part_cap * 4, 16);
+      p->d_part = nullptr;
+    }
+    st = dalloc(p, (void**)&p->d_part, need * 4);
+    if (st) return st;
+    p->part_cap = need;
+  }
+  SPM_CUDA(cudaStreamSynchronize(p->stream));  // host vectors may change after return
+  return SPM_OK;
+}
+
+static int check_plan(spmttkrp_plan* p, bool need_device = true) {
+  if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
+  if (need_device && p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
+  return SPM_OK;
+}
+
+static int check_factors(const spmttkrp_plan* p, const void* const* f, int skip) {
+  if (!f) return fail(SPM_ERR_INVALID_ARG, "factors array is null");
+  for (int k = 0; k < p->N; ++k)
+    if (k != skip && !f[k]) return fail(SPM_ERR_INVALID_ARG, "null factor pointer");
+  return SPM_OK;
+}
+
+// One remap-only pass of the working copy: mode cur_mode -> cur_mode + 1.
+static int remap_step(spmttkrp_plan* p) {
+  const int m = p->cur_mode;
+  int st = launch_remap_only(p->d_elem[p->cur_buf], p->d_elem[1 - p->cur_buf],
+                             p->md[(size_t)m].next_pos, p->nnz, p->es, p->stream);
+  if (st) return st;
+  p->cur_buf ^= 1;
+  p->cur_mode = (m + 1) % p->N;
+  return SPM_OK;
+}
+
+static int check_device_word(spmttkrp_plan* p) {
+  SPM_CUDA(cudaStreamSynchronize(p->stream));
+  int h = 0;
+  SPM_CUDA(cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    SPM_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+    return fail(SPM_ERR_TIMEOUT, "a bounded device wait gave up (bulk copy did not complete)");
+  }
+  return SPM_OK;
+}
+
+// Mode-n fused compute + remap on an explicit element copy pair.
+int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
+             const uint8_t* ein, uint8_t* eout, const float* scale) {
+  if (p->nnz == 0) return launch_zero_rows(out, p->dims[(size_t)mode], p->R, p->stream);
+  const ModeDev& d = p->md[(size_t)mode];
+  MttkrpArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.elems_in = ein;
+  a.elems_out = eout;
+  a.next_pos = d.next_pos;
+  a.blkinfo = d.blkinfo;
+  a.nblk = d.nblk;
+  for (int k = 0; k < p->N; ++k) a.factors[k] = factors[k];
+  a.out = out;
+  a.out_rows = p->dims[(size_t)mode];
+  a.R = p->R;
+  a.mode = mode;
+  a.nmodes = p->N;
+  a.es = p->es;
+  a.tile = p->tile;
+  a.part = p->d_part;
+  a.last_row = d.last_row;
+  a.err = p->d_err;
+  a.scale = scale;
+  a.dtype = p->dtype;
+  int st = launch_mttkrp(a, p->stream);
+  if (st) return st;
+  return launch_fixup(p->d_part, d.splits, d.nsplit, out, a.out_rows, p->R, scale, p->stream);
+}
+
+int compute_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out) {
+  while (p->cur_mode != mode) {
+    int st = remap_step(p);
+    if (st) return st;
+  }
+  int st = run_mode(p, mode, factors, out, p->d_elem[p->cur_buf], p->d_elem[1 - p->cur_buf],
+                    nullptr);
+  if (st) return st;
+  if (p->nnz > 0) p->cur_buf ^= 1;
+  p->cur_mode = (mode + 1) % p->N;
+  return SPM_OK;
+}
+
+static int sweep_eager(spmttkrp_plan* p, const void* const* factors, float* const* outs) {
+  const int start = p->cur_mode;
+  for (int i = 0; i < p->N; ++i) {
+    const int n = (start + i) % p->N;
+    int st = compute_mode(p, n, factors, outs[n]);
+    if (st) return st;
+  }
+  return SPM_OK;
+}
+
+}  // namespace spm
+
+using namespace spm;
+
+extern "C" {
+
+int spmttkrp_version(void) { return 100; }
+
+const char* spmttkrp_last_error(void) { return g_last_error.c_str(); }
+
+int spmttkrp_opts_init(spmttkrp_opts_t* o) {
+  if (!o) return fail(SPM_ERR_INVALID_ARG, "opts is null");
+  std::memset(o, 0, sizeof(*o));
+  return SPM_OK;
+}
+
+int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* vals,
+                         int64_t nnz, const int64_t* dims, int nmodes, int rank,
+                         const spmttkrp_opts_t* opts) {
+  if (!out) return fail(SPM_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (nmodes < 2) return fail(SPM_ERR_INVALID_ARG, "nmodes must be >= 2");
+  if (nmodes > kMaxModes) return fail(SPM_ERR_UNSUPPORTED, "nmodes > 16");
+  if (rank < 1) return fail(SPM_ERR_INVALID_ARG, "rank must be >= 1");
+  if (rank > kMaxRank) return fail(SPM_ERR_UNSUPPORTED, "rank > 256");
+  if (nnz < 0) return fail(SPM_ERR_INVALID_ARG, "nnz < 0");
+  if (nnz >= (int64_t(1) << 31) - 4) return fail(SPM_ERR_UNSUPPORTED, "nnz >= 2^31");
+  if (!dims) return fail(SPM_ERR_INVALID_ARG, "dims is null");
+  if (nnz > 0 && (!coo || !vals)) return fail(SPM_ERR_INVALID_ARG, "coo or vals is null");
+  for (int k = 0; k < nmodes; ++k) {
+    if (dims[k] < 1) return fail(SPM_ERR_INVALID_ARG, "dims[k] must be >= 1");
+    if (dims[k] > 2147483647LL) return fail(SPM_ERR_UNSUPPORTED, "dims[k] > 2^31-1");
+  }
+  spmttkrp_opts_t o;
+  spmttkrp_opts_init(&o);
+  if (opts) o = *opts;
+  if (o.factor_dtype != SPM_DTYPE_F32 && o.factor_dtype != SPM_DTYPE_BF16)
+    return fail(SPM_ERR_INVALID_ARG, "factor_dtype must be F32 or BF16");
+  if (o.partition != 0)
+    return fail(SPM_ERR_UNSUPPORTED, "only the contiguous split (partition 0) is built");
+  if (o.tile != 0 && o.tile != 256 && o.tile != 512 && o.tile != 1024)
+    return fail(SPM_ERR_INVALID_ARG, "tile must be 0, 256, 512 or 1024");
+  if (o.nblk < 0) return fail(SPM_ERR_INVALID_ARG, "nblk must be >= 0");
+
+  spmttkrp_plan* p = new (std::nothrow) spmttkrp_plan();
+  if (!p) return fail(SPM_ERR_OOM, "host allocation failed");
+  p->N = nmodes;
+  p->R = rank;
+  p->nnz = nnz;
+  p->dtype = o.factor_dtype;
+  p->tile = o.tile ? o.tile : 512;
+  p->checks = o.checks;
+  p->host_only = o.host_only;
+  p->max_bytes = o.max_bytes;
+  p->stream = (cudaStream_t)o.stream;
+  p->dims.assign(dims, dims + nmodes);
+  p->es = ((4 * nmodes + 4) + 15) & ~15;
+  // keep the staged tiles within shared memory for wide elements
+  while (p->tile > 256 && mttkrp_smem_bytes(p->es, p->tile, p->R, p->dtype) > 200 * 1024)
+    p->tile /= 2;
+  if (!p->host_only) {
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "cudaGetDevice");
+    }
+  }
+  int st;
+  try {
+    st = build_host_plan(p, coo, vals, o.nblk);
+  } catch (const std::bad_alloc&) {
+    st = fail(SPM_ERR_OOM, "host allocation failed while planning");
+  }
+  if (st) {
+    delete p;
+    return st;
+  }
+  if (!p->host_only) {
+    const int N = p->N;
+    p->md.assign((size_t)N, ModeDev());
+    const size_t eb = (size_t)p->nnz * p->es;
+    st = dalloc(p, (void**)&p->d_elem[0], eb);
+    if (!st) st = dalloc(p, (void**)&p->d_elem[1], eb);
+    if (!st) st = dalloc(p, (void**)&p->d_err, sizeof(int));
+    if (!st) {
+      cudaError_t e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
+      if (e == cudaSuccess && eb)
+        e = cudaMemcpyAsync(p->d_elem[0], p->h_elems.data(), eb, cudaMemcpyHostToDevice,
+                            p->stream);
+      if (e != cudaSuccess) st = cuda_fail(e, "upload of the working copy");
+    }
+    for (int n = 0; n < N && !st; ++n) {
+      ModeDev& d = p->md[(size_t)n];
+      st = dalloc(p, (void**)&d.next_pos, ((size_t)p->nnz + 4) * sizeof(int32_t));
+      if (!st) {
+        cudaError_t e = cudaMemsetAsync(d.next_pos, 0, ((size_t)p->nnz + 4) * 4, p->stream);
+        if (e == cudaSuccess && p->nnz)
+          e = cudaMemcpyAsync(d.next_pos, p->h_next_pos[(size_t)n].data(),
+                              (size_t)p->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "upload of next_pos");
+      }
+      if (!st) st = upload_mode_tables(p, n);
+    }
+    if (!st) {
+      cudaError_t e = cudaStreamSynchronize(p->stream);
+      if (e != cudaSuccess) st = cuda_fail(e, "plan upload");
+    }
+    if (st) {
+      spmttkrp_plan_destroy(p);
+      return st;
+    }
+    // the device holds the data now
+    std::vector<uint8_t>().swap(p->h_elems);
+    std::vector<std::vector<int32_t>>().swap(p->h_next_pos);
+  }
+  *out = p;
+  return SPM_OK;
+}
+
+int spmttkrp_plan_destroy(spmttkrp_plan_t p) {
+  if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
+  if (!p->host_only) cudaStreamSynchronize(p->stream);
+  for (auto& g : p->sweep_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& g : p->als_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (int i = 0; i < 3; ++i) dfree(p->d_elem[i]);
+  for (auto& d : p->md) {
+    dfree(d.next_pos);
+    dfree(d.blkinfo);
+    dfree(d.splits);
+  }
+  dfree(p->d_part);
+  dfree(p->d_err);
+  dfree(p->d_M);
+  dfree(p->d_gram);
+  dfree(p->d_red);
+  dfree(p->d_scal);
+  dfree(p->d_vinv);
+  p->destroyed = true;
+  delete p;
+  return SPM_OK;
+}
+
+int spmttkrp_set_stream(spmttkrp_plan_t p, void* stream) {
+  int st = check_plan(p, false);
+  if (st) return st;
+  p->stream = (cudaStream_t)stream;
+  return SPM_OK;
+}
+
+int spmttkrp_remap(spmttkrp_plan_t p, int mode) {
+  int st = check_plan(p);
+  if (st) return st;
+  if (mode < 0 || mode >= p->N) return fail(SPM_ERR_INVALID_ARG, "mode out of range");
+  while (p->cur_mode != mode) {
+    st = remap_step(p);
+    if (st) return st;
+  }
+  return SPM_OK;
+}
+
+int spmttkrp_compute(spmttkrp_plan_t p, int mode, const void* const* factors, float* out) {
+  int st = check_plan(p);
+  if (st) return st;
+  if (mode < 0 || mode >= p->N) return fail(SPM_ERR_INVALID_ARG, "mode out of range");
+  st = check_factors(p, factors, mode);
+  if (st) return st;
+  if (!out) return fail(SPM_ERR_INVALID_ARG, "out is null");
+  st = compute_mode(p, mode, factors, out);
+  if (st) return st;
+  if (p->checks) return check_device_word(p);
+  return SPM_OK;
+}
+
+int spmttkrp_sweep(spmttkrp_plan_t p, const void* const* factors, float* const* outs,
+                   int flags) {
+  int st = check_plan(p);
+  if (st) return st;
+  st = check_factors(p, factors, -1);
+  if (st) return st;
+  if (!outs) return fail(SPM_ERR_INVALID_ARG, "outs is null");
+  for (int k = 0; k < p->N; ++k)
+    if (!outs[k]) return fail(SPM_ERR_INVALID_ARG, "null output pointer");
+  if (!(flags & SPM_SWEEP_GRAPH)) {
+    st = sweep_eager(p, factors, outs);
+    if (st) return st;
+    return p->checks ? check_device_word(p) : SPM_OK;
+  }
+  // graph replay: one captured graph per (pointers, buffer parity, start mode)
+  std::vector<const void*> key;
+  for (int k = 0; k < p->N; ++k) key.push_back(factors[k]);
+  for (int k = 0; k < p->N; ++k) key.push_back(outs[k]);
+  key.push_back((const void*)(intptr_t)(p->cur_buf * 64 + p->cur_mode));
+  key.push_back((const void*)p->stream);
+  GraphCache* hit = nullptr;
+  for (auto& g : p->sweep_graphs)
+    if (g.key == key) hit = &g;
+  const int buf0 = p->cur_buf, mode0 = p->cur_mode;
+  if (!hit) {
+    // first run eagerly: configures every kernel outside of stream capture
+    st = sweep_eager(p, factors, outs);
+    if (st) return st;
+    const int buf1 = p->cur_buf, mode1 = p->cur_mode;
+    p->cur_buf = buf0;
+    p->cur_mode = mode0;
+    cudaGraph_t g = nullptr;
+    SPM_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    st = sweep_eager(p, factors, outs);
+    cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    p->cur_buf = buf1;
+    p->cur_mode = mode1;
+    if (st) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(sweep)");
+    GraphCache gc;
+    gc.key = key;
+    e = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(sweep)");
+    if (p->sweep_graphs.size() >= 8) {
+      cudaGraphExecDestroy(p->sweep_graphs.front().exec);
+      p->sweep_graphs.erase(p->sweep_graphs.begin());
+    }
+    p->sweep_graphs.push_back(gc);
+    return p->checks ? check_device_word(p) : SPM_OK;
+  }
+  SPM_CUDA(cudaGraphLaunch(hit->exec, p->stream));
+  if (p->nnz > 0 && (p->N & 1)) p->cur_buf ^= 1;
+  // the start mode is unchanged after a full cycle of N modes
+  return p->checks ? check_device_word(p) : SPM_OK;
+}
+
+int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t bytes) {
+  int st = check_plan(p, false);
+  if (st) return st;
+  if (!dst) return fail(SPM_ERR_INVALID_ARG, "dst is null");
+  const int N = p->N;
+  const int64_t nnz = p->nnz;
+  auto need = [&](size_t b) -> int {
+    return bytes < b ? fail(SPM_ERR_INVALID_ARG, "destination too small") : SPM_OK;
+  };
+  if (what != SPM_Q_INFO && what != SPM_Q_ELEMS && what != SPM_Q_VALS && (mode < 0 || mode >= N))
+    return fail(SPM_ERR_INVALID_ARG, "mode out of range");
+  switch (what) {
+    case SPM_Q_INFO: {
+      if ((st = need(16 * sizeof(int64_t)))) return st;
+      int m = (mode >= 0 && mode < N) ? mode : 0;
+      int64_t* o = (int64_t*)dst;
+      std::memset(o, 0, 16 * sizeof(int64_t));
+      o[0] = nnz;
+      o[1] = N;
+      o[2] = p->R;
+      o[3] = p->es;
+      o[4] = p->cur_mode;
+      o[5] = p->dtype;
+      o[6] = p->tile;
+      o[7] = p->mh[(size_t)m].nblk;
+      o[8] = (int64_t)p->mh[(size_t)m].splits.size();
+      int64_t launches = 0;
+      for (int n = 0; n < N; ++n) launches += 1 + (p->mh[(size_t)n].splits.empty() ? 0 : 1);
+      o[9] = nnz > 0 ? launches : N;
+      o[10] = (int64_t)p->dev_bytes;
+      o[11] = p->cur_buf;
+      o[12] = p->host_only;
+      o[13] = p->num_sms;
+      std::memcpy(&o[14], &p->normx2, 8);
+      o[15] = lane_config(p->R, p->dtype, true).L;
+      return SPM_OK;
+    }
+    case SPM_Q_NEXT_POS: {
+      if ((st = need((size_t)nnz * 4))) return st;
+      if (nnz == 0) return SPM_OK;
+      if (p->host_only) {
+        std::memcpy(dst, p->h_next_pos[(size_t)mode].data(), (size_t)nnz * 4);
+        return SPM_OK;
+      }
+      SPM_CUDA(cudaStreamSynchronize(p->stream));
+      SPM_CUDA(cudaMemcpy(dst, p->md[(size_t)mode].next_pos, (size_t)nnz * 4,
+                          cudaMemcpyDeviceToHost));
+      return SPM_OK;
+    }
+    case SPM_Q_BOUNDS: {
+      const ModeHost& h = p->mh[(size_t)mode];
+      if ((st = need(h.bounds.size() * 8))) return st;
+      std::memcpy(dst, h.bounds.data(), h.bounds.size() * 8);
+      return SPM_OK;
+    }
+    case SPM_Q_SPLITS: {
+      const ModeHost& h = p->mh[(size_t)mode];
+      if ((st = need(h.splits.size() * 24))) return st;
+      int64_t* o = (int64_t*)dst;
+      for (size_t i = 0; i < h.splits.size(); ++i) {
+        o[3 * i] = h.splits[i].row;
+        o[3 * i + 1] = h.splits[i].first_blk;
+        o[3 * i + 2] = h.splits[i].last_blk;
+      }
+      return SPM_OK;
+    }
+    case SPM_Q_ELEMS:
+    case SPM_Q_VALS: {
+      const size_t per = (what == SPM_Q_ELEMS) ? (size_t)N * 4 : 4;
+      if ((st = need((size_t)nnz * per))) return st;
+      if (nnz == 0) return SPM_OK;
+      std::vector<uint8_t> tmp;
+      const uint8_t* src;
+      if (p->host_only) {
+        src = p->h_elems.data();
+      } else {
+        tmp.resize((size_t)nnz * p->es);
+        SPM_CUDA(cudaStreamSynchronize(p->stream));
+        SPM_CUDA(cudaMemcpy(tmp.data(), p->d_elem[p->cur_buf], tmp.size(), cudaMemcpyDeviceToHost));
+        src = tmp.data();
+      }
+      uint8_t* o = (uint8_t*)dst;
+      for (int64_t q = 0; q < nnz; ++q) {
+        const uint8_t* e = src + (size_t)q * p->es;
+        if (what == SPM_Q_ELEMS)
+          std::memcpy(o + (size_t)q * N * 4, e, (size_t)N * 4);
+        else
+          std::memcpy(o + (size_t)q * 4, e + (size_t)N * 4, 4);
+      }
+      return SPM_OK;
+    }
+    default:
+      return fail(SPM_ERR_INVALID_ARG, "unknown query");
+  }
+}
+
+int spmttkrp_device_status(spmttkrp_plan_t p) {
+  int st = check_plan(p);
+  if (st) return st;
+  return check_device_word(p);
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// engine.h - internal declarations shared by the host plan builder, the
+// kernels and the C ABI of the all-mode sparse MTTKRP engine.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/spmttkrp.h"
+
+namespace spm {
+
+constexpr int kMaxModes = 16;
+constexpr int kMaxRank = 256;
+constexpr int kThreads = 256;  // threads per CTA of the fused kernel
+
+// Per-block descriptor of one mode's contiguous split (int4 on the device):
+//   x = first position, y = one past the last position,
+//   z = row of position x-1 (the row before the block; -1 for none),
+//   w = flags: bit0 = the block's first row started in an earlier block,
+//              bit1 = the block's last row continues into a later block.
+enum { BLK_HEAD_SPLIT = 1, BLK_TAIL_SPLIT = 2 };
+
+// Split-row descriptor (int4 pairs on the device):
+//   a = {row, first_blk, last_blk, slot of first_blk (0 or 1)}
+//   b = {row before this row (-1 for none), 1 if it is the last nonempty row, 0, 0}
+struct SplitRow {
+  int row, first_blk, last_blk, first_slot;
+  int prev_row, is_last, pad0, pad1;
+};
+
+// Host-side result of planning one mode.
+struct ModeHost {
+  int nblk = 0;
+  std::vector<int64_t> bounds;     // nblk + 1
+  std::vector<int32_t> blkinfo;    // 4 * nblk
+  std::vector<SplitRow> splits;    // ascending rows
+  int last_row = -1;               // row of position nnz-1
+};
+
+// Device tables of one mode.
+struct ModeDev {
+  int nblk = 0;
+  int nsplit = 0;
+  int last_row = -1;
+  int4* blkinfo = nullptr;
+  SplitRow* splits = nullptr;
+  int32_t* next_pos = nullptr;  // nnz (+4 padding ints)
+};
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> key;
+};
+
+}  // namespace spm
+
+struct spmttkrp_plan {
+  int N = 0, R = 0, dtype = 0, tile = 512, checks = 0, host_only = 0;
+  int64_t nnz = 0;
+  int es = 16;  // element stride in bytes: {int32 idx[N]; float val}, rounded up to 16
+  std::vector<int64_t> dims;
+  size_t max_bytes = 0, dev_bytes = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 148;
+
+  // host copies kept for re-partitioning (row starts per mode) and queries
+  std::vector<std::vector<int64_t>> row_start;   // N x (dims[n] + 1)
+  std::vector<std::vector<int32_t>> h_next_pos;  // host-only plans keep these
+  std::vector<spm::ModeHost> mh;                 // per mode
+  std::vector<uint8_t> h_elems;                  // host-only plans: mode-0 working copy
+  double normx2 = 0.0;                           // sum of squared values (FP64)
+
+  // device state
+  uint8_t* d_elem[3] = {nullptr, nullptr, nullptr};  // working copy ping/pong + residual copy
+  int cur_buf = 0;   // which of d_elem[0..1] holds the working copy
+  int cur_mode = 0;  // canonical order the working copy is in
+  std::vector<spm::ModeDev> md;
+  float* d_part = nullptr;   // split-row partials: max nblk x 2 x R
+  size_t part_cap = 0;       // floats
+  int* d_err = nullptr;      // device error word
+  // ALS / CP-loss scratch
+  float* d_M = nullptr;      // max_n dims[n] x R
+  double* d_gram = nullptr;  // N x R x R
+  double* d_red = nullptr;   // reduction partials
+  size_t red_cap = 0;
+  double* d_scal = nullptr;  // small FP64 scalars (loss, fit terms)
+  float* d_vinv = nullptr;   // R x R
+  int res_valid = 0;         // residual copy d_elem[2] is current
+  int res_mode = 0;          // order the residual copy is in
+  int res_buf = 2;           // which buffer holds the residual copy (2 or the free one)
+  std::vector<spm::GraphCache> sweep_graphs;  // by parity
+  std::vector<spm::GraphCache> als_graphs;
+  bool destroyed = false;
+};
+
+namespace spm {
+
+// ---- error reporting (thread-local last error) ----
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+#define SPM_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return spm::cuda_fail(_e, #call); \
+  } while (0)
+
+// ---- host planning (plan_host.cpp) ----
+int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int nblk_opt);
+int partition_mode(const spmttkrp_plan* p, int n, int nblk, ModeHost* out);
+int default_nblk(int64_t nnz, int num_sms);
+
+// ---- kernel launchers (kernels_*.cu) ----
+struct MttkrpArgs {
+  const uint8_t* elems_in;
+  uint8_t* elems_out;      // null: no remap
+  const int32_t* next_pos;
+  const int4* blkinfo;
+  int nblk;
+  const void* factors[kMaxModes];
+  float* out;
+  int64_t out_rows;
+  int R, mode, nmodes, es, tile;
+  float* part;
+  int last_row;
+  int* err;
+  const float* scale;      // device scalar multiplier or null
+  int dtype;
+};
+int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
+int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* out,
+                 int64_t out_rows, int R, const float* scale, cudaStream_t s);
+int launch_zero_rows(float* out, int64_t rows, int R, cudaStream_t s);
+int launch_remap_only(const uint8_t* in, uint8_t* out, const int32_t* next_pos, int64_t nnz,
+                      int es, cudaStream_t s);
+size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype);
+
+}  // namespace spm

@@ -1,0 +1,328 @@
+// plan_host.cpp - host-side planning of the all-mode sparse MTTKRP engine.
+//
+// This is the preprocessing step of the paper (Section 3.4-3.5; the
+// evaluation's preprocessing is also done on the CPU): it sorts the nonzeros
+// into every mode's canonical order, computes the remap ids that the dynamic
+// remap (Section 3.1, Algorithm 3) scatters by, and cuts every mode into
+// blocks that own disjoint output rows (Observation 2).
+//
+// Canonical order of mode n: lexicographic by K_n = (i_n, i_{n-1}, ..., i_0,
+// i_{N-1}, ..., i_{n+1}).  A stable sort of the mode-n order by i_{n+1} is the
+// mode-(n+1) order, so every order follows from the previous one by one
+// stable counting pass, and next_pos_n is exactly the destination of that
+// pass.  All sorts here are stable LSD radix passes (16-bit digits at most),
+// parallelised over contiguous slices with per-slice histograms, so the
+// result does not depend on the thread count.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <thread>
+#include <vector>
+
+#include "engine.h"
+
+namespace spm {
+
+static int pick_threads(int64_t work) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int t = hw ? (int)hw : 4;
+  if (t > 32) t = 32;
+  if (work < (1 << 16)) t = 1;
+  return t;
+}
+
+// Runs f(slice_index, begin, end) over T contiguous slices of [0, n).
+static void parallel_slices(int T, int64_t n, const std::function<void(int, int64_t, int64_t)>& f) {
+  if (T <= 1) {
+    f(0, 0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(T);
+  for (int t = 0; t < T; ++t) {
+    int64_t b = n * t / T, e = n * (t + 1) / T;
+    th.emplace_back([&f, t, b, e] { f(t, b, e); });
+  }
+  for (auto& x : th) x.join();
+}
+
+static int bits_for(int64_t dim) {
+  int b = 1;
+  while (b < 31 && (int64_t(1) << b) < dim) ++b;
+  return b;
+}
+
+// One stable counting pass: out = in ordered by digit ((key[in[p]] >> shift) & mask).
+static void radix_pass(const int32_t* key, const int32_t* in, int32_t* out, int64_t n, int shift,
+                       int bits, int T) {
+  const int D = 1 << bits;
+  const uint32_t mask = (uint32_t)D - 1;
+  std::vector<int64_t> hist((size_t)T * D, 0);
+  parallel_slices(T, n, [&](int t, int64_t b, int64_t e) {
+    int64_t* h = &hist[(size_t)t * D];
+    for (int64_t p = b; p < e; ++p) h[((uint32_t)key[in[p]] >> shift) & mask]++;
+  });
+  int64_t run = 0;
+  for (int d = 0; d < D; ++d)
+    for (int t = 0; t < T; ++t) {
+      int64_t c = hist[(size_t)t * D + d];
+      hist[(size_t)t * D + d] = run;
+      run += c;
+    }
+  parallel_slices(T, n, [&](int t, int64_t b, int64_t e) {
+    int64_t* h = &hist[(size_t)t * D];
+    for (int64_t p = b; p < e; ++p) {
+      int32_t v = in[p];
+      out[h[((uint32_t)key[v] >> shift) & mask]++] = v;
+    }
+  });
+}
+
+// Stable sort of perm (element ids) by key[] in [0, dim): LSD passes low digit first.
+static void stable_sort_by(const int32_t* key, int64_t dim, std::vector<int32_t>& perm,
+                           std::vector<int32_t>& tmp, int T) {
+  int bits = bits_for(dim);
+  int passes = (bits + 15) / 16;
+  int per = (bits + passes - 1) / passes;
+  int shift = 0;
+  for (int ps = 0; ps < passes; ++ps) {
+    int b = std::min(per, bits - shift);
+    radix_pass(key, perm.data(), tmp.data(), (int64_t)perm.size(), shift, b, T);
+    perm.swap(tmp);
+    shift += b;
+  }
+}
+
+int default_nblk(int64_t nnz, int num_sms) {
+  if (nnz <= 0) return 1;
+  // about 32K nonzeros per block for large tensors, at least 4 blocks per SM
+  // while each keeps >= 256 nonzeros
+  int64_t big = (nnz + 32767) / 32768;
+  int64_t small = std::min<int64_t>((int64_t)num_sms * 4, (nnz + 255) / 256);
+  int64_t nb = std::max<int64_t>(big, small);
+  nb = std::max<int64_t>(1, std::min<int64_t>(nb, 1 << 20));
+  return (int)nb;
+}
+
+// Position -> index of the nonempty row holding it (ustart ascending, size nu+1).
+static inline int64_t row_index_of(const std::vector<int64_t>& ustart, int64_t pos) {
+  return (int64_t)(std::upper_bound(ustart.begin(), ustart.end(), pos) - ustart.begin()) - 1;
+}
+
+// Contiguous split of one mode with heavy-row splitting (the engine's reading
+// of Section 3.4 for rows heavier than a block):
+//   T = ceil(nnz / nblk); for j = 1..nblk-1, t = min(j*T, nnz), r = the row
+//   holding t.  t == start(r): boundary t.  deg(r) <= T: snap to start(r) or
+//   end(r), whichever is nearer (ties to start).  Else: boundary t, r is split.
+int partition_mode(const spmttkrp_plan* p, int n, int nblk, ModeHost* out) {
+  if (nblk < 1) return fail(SPM_ERR_INVALID_ARG, "nblk must be >= 1");
+  const int64_t nnz = p->nnz;
+  const std::vector<int64_t>& us = p->row_start[n];   // nonempty-row starts (+nnz)
+  const std::vector<int64_t>& ur = p->row_start[p->N + n];  // nonempty-row ids
+  ModeHost m;
+  m.nblk = nblk;
+  m.bounds.assign((size_t)nblk + 1, 0);
+  m.bounds[nblk] = nnz;
+  if (nnz > 0) {
+    const int64_t T = (nnz + nblk - 1) / nblk;
+    for (int j = 1; j < nblk; ++j) {
+      int64_t t = std::min<int64_t>((int64_t)j * T, nnz);
+      if (t >= nnz) {
+        m.bounds[j] = nnz;
+        continue;
+      }
+      int64_t u = row_index_of(us, t);
+      int64_t s = us[u], e = us[u + 1];
+      if (t == s)
+        m.bounds[j] = t;
+      else if (e - s <= T)
+        m.bounds[j] = (t - s <= e - t) ? s : e;
+      else
+        m.bounds[j] = t;
+    }
+    m.last_row = (int)ur.back();
+  }
+  // per-block descriptors
+  m.blkinfo.assign((size_t)nblk * 4, 0);
+  for (int b = 0; b < nblk; ++b) {
+    int64_t lo = m.bounds[b], hi = m.bounds[b + 1];
+    int32_t* bi = &m.blkinfo[(size_t)b * 4];
+    bi[0] = (int32_t)lo;
+    bi[1] = (int32_t)hi;
+    bi[2] = -1;
+    bi[3] = 0;
+    if (lo < hi) {
+      int64_t ulo = row_index_of(us, lo);
+      if (lo > 0) {
+        int64_t uprev = row_index_of(us, lo - 1);
+        bi[2] = (int32_t)ur[uprev];
+        if (uprev == ulo) bi[3] |= BLK_HEAD_SPLIT;
+      }
+      if (hi < nnz) {
+        if (row_index_of(us, hi) == row_index_of(us, hi - 1)) bi[3] |= BLK_TAIL_SPLIT;
+      }
+    }
+  }
+  // split rows: a boundary strictly inside a row
+  int64_t last_u = -1;
+  for (int j = 1; j < nblk; ++j) {
+    int64_t t = m.bounds[j];
+    if (t <= 0 || t >= nnz) continue;
+    int64_t u = row_index_of(us, t);
+    if (us[u] < t && t < us[u + 1] && u != last_u) {
+      SplitRow sr;
+      int64_t s = us[u], e = us[u + 1];
+      sr.row = (int)ur[u];
+      sr.first_blk =
+          (int)(std::upper_bound(m.bounds.begin(), m.bounds.end(), s) - m.bounds.begin()) - 1;
+      sr.last_blk =
+          (int)(std::upper_bound(m.bounds.begin(), m.bounds.end(), e - 1) - m.bounds.begin()) - 1;
+      sr.first_slot = (m.bounds[sr.first_blk] == s) ? 0 : 1;
+      sr.prev_row = u > 0 ? (int)ur[u - 1] : -1;
+      sr.is_last = (e == nnz) ? 1 : 0;
+      sr.pad0 = sr.pad1 = 0;
+      m.splits.push_back(sr);
+      last_u = u;
+    }
+  }
+  *out = std::move(m);
+  return SPM_OK;
+}
+
+int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int nblk_opt) {
+  const int N = p->N;
+  const int64_t nnz = p->nnz;
+  const int T = pick_threads(nnz);
+
+  // key columns (int32) in input order, with range validation
+  std::vector<std::vector<int32_t>> key(N);
+  for (int k = 0; k < N; ++k) key[k].resize((size_t)nnz);
+  std::atomic<int64_t> bad{-1};
+  parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
+    for (int64_t q = b; q < e; ++q)
+      for (int k = 0; k < N; ++k) {
+        int64_t v = coo[q * N + k];
+        if (v < 0 || v >= p->dims[k]) {
+          int64_t expect = -1;
+          bad.compare_exchange_strong(expect, q);
+          return;
+        }
+        key[k][q] = (int32_t)v;
+      }
+  });
+  if (bad.load() >= 0)
+    return fail(SPM_ERR_INDEX_RANGE,
+                "coordinate out of range at nonzero " + std::to_string(bad.load()));
+
+  // sum of squared values, fixed 1M chunks added in order (deterministic)
+  {
+    const int64_t C = 1 << 20;
+    int64_t nchunk = (nnz + C - 1) / C;
+    std::vector<double> part((size_t)std::max<int64_t>(nchunk, 1), 0.0);
+    parallel_slices(std::min<int64_t>(T, std::max<int64_t>(nchunk, 1)), nchunk,
+                    [&](int, int64_t b, int64_t e) {
+                      for (int64_t c = b; c < e; ++c) {
+                        double s = 0.0;
+                        for (int64_t q = c * C; q < std::min(nnz, (c + 1) * C); ++q)
+                          s += (double)vals[q] * (double)vals[q];
+                        part[(size_t)c] = s;
+                      }
+                    });
+    double s = 0.0;
+    for (int64_t c = 0; c < nchunk; ++c) s += part[(size_t)c];
+    p->normx2 = s;
+  }
+
+  // mode-0 order: LSD over keys i_1, i_2, ..., i_{N-1}, then i_0 (primary)
+  std::vector<int32_t> perm0((size_t)nnz), tmp((size_t)nnz);
+  for (int64_t q = 0; q < nnz; ++q) perm0[(size_t)q] = (int32_t)q;
+  for (int j = 1; j <= N; ++j) {
+    int k = j % N;
+    stable_sort_by(key[k].data(), p->dims[k], perm0, tmp, T);
+  }
+
+  // duplicates: equal neighbours in mode-0 order
+  std::atomic<int64_t> dup{-1};
+  parallel_slices(T, std::max<int64_t>(nnz - 1, 0), [&](int, int64_t b, int64_t e) {
+    for (int64_t q = b; q < e; ++q) {
+      int32_t x = perm0[(size_t)q], y = perm0[(size_t)q + 1];
+      bool same = true;
+      for (int k = 0; k < N && same; ++k) same = key[k][x] == key[k][y];
+      if (same) {
+        int64_t expect = -1;
+        dup.compare_exchange_strong(expect, q);
+        return;
+      }
+    }
+  });
+  if (dup.load() >= 0) return fail(SPM_ERR_DUPLICATE, "duplicate coordinate in the COO input");
+
+  // working copy in mode-0 order: {int32 idx[N]; float val; zero padding}
+  const int es = p->es;
+  p->h_elems.assign((size_t)nnz * es, 0);
+  parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
+    for (int64_t q = b; q < e; ++q) {
+      int32_t x = perm0[(size_t)q];
+      int32_t* d = reinterpret_cast<int32_t*>(&p->h_elems[(size_t)q * es]);
+      for (int k = 0; k < N; ++k) d[k] = key[k][x];
+      std::memcpy(&d[N], &vals[x], 4);
+    }
+  });
+
+  // per mode: nonempty rows and their starts, and next_pos_n
+  p->row_start.assign((size_t)2 * N, {});
+  p->h_next_pos.assign((size_t)N, {});
+  std::vector<int32_t> cur = perm0, inv((size_t)nnz);
+  for (int n = 0; n < N; ++n) {
+    // nonempty rows of mode n in the mode-n order `cur`
+    const int32_t* kn = key[n].data();
+    std::vector<int64_t> cnt((size_t)T + 1, 0);
+    parallel_slices(T, nnz, [&](int t, int64_t b, int64_t e) {
+      int64_t c = 0;
+      for (int64_t q = b; q < e; ++q)
+        if (q == 0 || kn[cur[(size_t)q]] != kn[cur[(size_t)q - 1]]) ++c;
+      cnt[(size_t)t + 1] = c;
+    });
+    for (int t = 0; t < T; ++t) cnt[(size_t)t + 1] += cnt[(size_t)t];
+    int64_t nu = cnt[(size_t)T];
+    std::vector<int64_t>& us = p->row_start[(size_t)n];
+    std::vector<int64_t>& ur = p->row_start[(size_t)N + n];
+    us.assign((size_t)nu + 1, nnz);
+    ur.assign((size_t)nu, 0);
+    parallel_slices(T, nnz, [&](int t, int64_t b, int64_t e) {
+      int64_t c = cnt[(size_t)t];
+      for (int64_t q = b; q < e; ++q)
+        if (q == 0 || kn[cur[(size_t)q]] != kn[cur[(size_t)q - 1]]) {
+          us[(size_t)c] = q;
+          ur[(size_t)c] = kn[cur[(size_t)q]];
+          ++c;
+        }
+    });
+    // next order: stable sort of the mode-n order by i_{n+1}
+    const int nx = (n + 1) % N;
+    std::vector<int32_t> nxt = cur;
+    stable_sort_by(key[nx].data(), p->dims[nx], nxt, tmp, T);
+    parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
+      for (int64_t q = b; q < e; ++q) inv[(size_t)nxt[(size_t)q]] = (int32_t)q;
+    });
+    std::vector<int32_t>& np = p->h_next_pos[(size_t)n];
+    np.resize((size_t)nnz);
+    parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
+      for (int64_t q = b; q < e; ++q) np[(size_t)q] = inv[(size_t)cur[(size_t)q]];
+    });
+    cur.swap(nxt);
+  }
+
+  // partitions
+  p->mh.assign((size_t)N, ModeHost());
+  for (int n = 0; n < N; ++n) {
+    int nb = nblk_opt > 0 ? nblk_opt : default_nblk(nnz, p->num_sms);
+    int st = partition_mode(p, n, nb, &p->mh[(size_t)n]);
+    if (st != SPM_OK) return st;
+  }
+  return SPM_OK;
+}
+
+}  // namespace spm

@@ -1,0 +1,136 @@
+"""C-ABI library checks that need no GPU: exported symbols, host-side planning
+(bit-exact against the oracle) and host-side error paths."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from paper_2405_08470_gb300 import Plan, SpmError, binding, declared_functions, lib
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def test_library_exports_every_declared_symbol():
+    L = lib()
+    names = declared_functions()
+    for must in ["spmttkrp_plan_create", "spmttkrp_plan_destroy", "spmttkrp_remap",
+                 "spmttkrp_compute", "spmttkrp_sweep", "cp_als_iter", "cp_loss_fwd",
+                 "cp_loss_bwd", "spmttkrp_autotune", "spmttkrp_plan_query",
+                 "spmttkrp_last_error", "spmttkrp_opts_init", "spmttkrp_set_stream",
+                 "spmttkrp_device_status", "spmttkrp_version"]:
+        assert must in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert L.spmttkrp_version() >= 100
+
+
+def _host_plan(coo, vals, dims, R=4, nblk=0):
+    return Plan(coo, vals, dims, R, nblk=nblk, host_only=True)
+
+
+@pytest.mark.parametrize("dims,nnz,skew,nblk", [
+    ((200, 150, 100), 5000, (0.0, 0.0, 0.0), 0),
+    ((50, 40, 30), 3000, (1.1, 1.1, 1.1), 17),
+    ((30, 20, 10, 8), 2500, (1.2, 1.2, 0.0, 0.0), 9),
+    ((12, 9, 7, 5, 4), 1500, (1.1,) * 5, 64),
+    ((9, 3), 20, (0.0, 0.0), 40),                   # nblk > nnz
+    ((6, 5, 4, 3, 3, 2, 2, 2, 2), 900, (0.0,) * 9, 5),  # 9 modes (runtime-N path)
+])
+def test_host_plan_matches_oracle_bit_exact(dims, nnz, skew, nblk):
+    coo, vals = synth.make_coo(dims, nnz, skew, seed=sum(dims))
+    c, v = coo.numpy(), vals.numpy()
+    p = _host_plan(c, v, dims, nblk=nblk)
+    N = len(dims)
+    idx, val = p.elements()
+    wi, wv = O.elements_in_order(c, v, 0)
+    assert np.array_equal(idx, wi) and np.array_equal(val, wv)
+    for n in range(N):
+        assert np.array_equal(p.next_pos(n), O.next_pos(c, n).astype(np.int32))
+        rows = c[O.canonical_order(c, n), n]
+        nb = p.info(n)["nblk"]
+        b = p.bounds(n)
+        assert np.array_equal(b, O.contiguous_partition(rows, nb))
+        assert np.array_equal(p.splits(n), O.split_rows(rows, b))
+    assert p.info()["normx2"] == pytest.approx(float(np.sum(v.astype(np.float64) ** 2)),
+                                               rel=1e-12)
+    p.close()
+
+
+def test_host_plan_heavy_single_row_split_everywhere():
+    coo = np.stack([np.zeros(1000, np.int64), np.arange(1000) % 50, np.arange(1000) // 50], 1)
+    vals = np.ones(1000, np.float32)
+    p = _host_plan(coo, vals, (3, 50, 20), nblk=8)
+    assert p.splits(0).tolist() == [[0, 0, 7]]
+    rows = coo[O.canonical_order(coo, 0), 0]
+    assert np.array_equal(p.bounds(0), O.contiguous_partition(rows, 8))
+
+
+def test_host_plan_empty_tensor():
+    p = _host_plan(np.zeros((0, 3), np.int64), np.zeros(0, np.float32), (4, 5, 6), nblk=3)
+    assert p.info()["nnz"] == 0
+    assert p.bounds(1).tolist() == [0, 0, 0, 0]
+
+
+@pytest.mark.parametrize("case,status", [
+    ("dup", -3), ("range", -2), ("neg", -2), ("nmodes", -1), ("rank0", -1), ("rank_big", -6),
+    ("tile", -1), ("dims0", -1), ("partition", -6), ("dtype", -1),
+])
+def test_host_error_paths(case, status):
+    coo = np.array([[0, 1, 2], [1, 1, 1], [2, 0, 0]], np.int64)
+    vals = np.ones(3, np.float32)
+    dims, R, kw = (3, 3, 3), 4, {}
+    if case == "dup":
+        coo[2] = coo[0]
+    elif case == "range":
+        coo[1, 2] = 3
+    elif case == "neg":
+        coo[1, 0] = -1
+    elif case == "nmodes":
+        coo, dims = coo[:, :1], (3,)
+    elif case == "rank0":
+        R = 0
+    elif case == "rank_big":
+        R = 257
+    elif case == "tile":
+        kw["tile"] = 300
+    elif case == "dims0":
+        dims = (3, 0, 3)
+    if case in ("partition", "dtype"):
+        L = lib()
+        o = binding.Opts()
+        L.spmttkrp_opts_init(ctypes.byref(o))
+        o.host_only = 1
+        if case == "partition":
+            o.partition = 1
+        else:
+            o.factor_dtype = 7
+        h = ctypes.c_void_p()
+        d = np.asarray(dims, np.int64)
+        st = L.spmttkrp_plan_create(ctypes.byref(h), coo.ctypes.data, vals.ctypes.data, 3,
+                                    d.ctypes.data_as(binding.I64P), 3, R, ctypes.byref(o))
+        assert st == status
+        assert L.spmttkrp_last_error()
+        return
+    with pytest.raises(SpmError) as ei:
+        Plan(coo, vals, dims, R, host_only=True, **kw)
+    assert ei.value.status == status
+
+
+def test_null_pointer_and_state_errors():
+    L = lib()
+    assert L.spmttkrp_plan_create(None, None, None, 0, None, 3, 4, None) == -1
+    h = ctypes.c_void_p()
+    d = np.asarray((3, 3, 3), np.int64)
+    assert L.spmttkrp_plan_create(ctypes.byref(h), None, None, 5, d.ctypes.data_as(binding.I64P),
+                                  3, 4, None) == -1
+    p = _host_plan(np.array([[0, 0, 0]]), np.ones(1, np.float32), (2, 2, 2))
+    # compute on a host-only plan is a state error, not a crash
+    assert L.spmttkrp_compute(p._h, 0, None, None) == -8
+    assert L.spmttkrp_remap(p._h, 5) == -8
+    p.close()
