@@ -1,0 +1,394 @@
+"""Benchmark: all-mode sparse MTTKRP sweep on a GB300 (one JSON line on stdout).
+
+A step is one all-mode sweep (Algorithm 5): for every mode n, the fused
+spMTTKRP + dynamic-remap kernel and, when the mode has split rows, the fix-up.
+Default workload: 3-mode 120000 x 90000 x 2000000 tensor, 100M distinct
+nonzeros with Zipf(1.1) index skew on every mode, FP32 values, rank 32, FP32
+factors (synthetic stand-in for the paper's FROSTT / recommender tensors).
+
+Usage:
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--rank R]
+                  [--dtype f32|bf16] [--impl mine|reference]
+Multi-GPU (one process per GPU via torchrun): independent replicas, one per
+rank (the sweep has no cross-GPU exchange in this build), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD_INDEX = {"c1": 0, "c2": 1, "c3": 2, "c4a": 3, "c4b": 3, "c5": 4}
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--rank", type=int, default=0)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--nnz", type=int, default=0, help="override nonzero count (small runs)")
+    ap.add_argument("--nblk", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload_tensors(name, nnz_override, device):
+    spec = synth.workload(name)
+    nnz = nnz_override or spec.nnz
+    coo, vals = synth.make_coo(spec.dims, nnz, spec.skew, spec.seed, device=device)
+    return spec, coo, vals
+
+
+def compulsory_bytes(dims, nnz, R, s, touched, N):
+    """Algorithmic bytes of mode n's fused pass (elements read + next_pos + remapped write,
+    each touched factor row once, output written once)."""
+    E = 4 * N + 4
+    out = []
+    for n in range(N):
+        b = nnz * (E + 4 + E)
+        b += sum(touched[k] * R * s for k in range(N) if k != n)
+        b += dims[n] * R * 4
+        out.append(b)
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2405_08470_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith("mttkrp_kernel") or f.startswith("kernels_"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, R, dtype):
+    """DRAM bytes per launch of the fused kernel from a committed ncu summary, if its
+    kernel digest matches the current sources (else null: counters are stale)."""
+    path = os.path.join(PROFILES, "mttkrp_remap_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_digest") != kernel_digest():
+        return None
+    key = f"{workload}_R{R}_{dtype}"
+    e = d.get("entries", {}).get(key)
+    return e.get("dram_bytes_per_launch_full") if e else None
+
+
+def cpu_oracle_sample(coo_h, vals_h, dims, R, target_s, seed):
+    """Time the FP64 oracle on the first S nonzeros (draw order) of the workload for all
+    modes; S grows until the run takes about target_s seconds."""
+    import oracle
+    F = [f.numpy() for f in synth.make_factors(dims, R, seed=seed)]
+    nnz = coo_h.shape[0]
+    S = min(nnz, 100_000)
+    while True:
+        t0 = time.perf_counter()
+        for n in range(len(dims)):
+            oracle.mttkrp(coo_h[:S], vals_h[:S], dims, F, n)
+        dt = time.perf_counter() - t0
+        if dt >= target_s * 0.5 or S >= nnz:
+            return S, dt
+        S = min(nnz, int(S * max(2.0, target_s / max(dt, 1e-3))))
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, timed on the host cores (bounded sample per step)."""
+    if rank != 0:
+        return
+    spec = synth.workload(args.workload)
+    R = args.rank or spec.ranks[0]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    sample_nnz = 400_000
+    coo, vals = synth.make_coo(spec.dims, args.nnz or spec.nnz, spec.skew, spec.seed, device=dev) \
+        if dev == "cuda" else synth.make_coo(spec.dims, sample_nnz, spec.skew, spec.seed)
+    nnz_full = args.nnz or spec.nnz
+    coo_h = coo[:sample_nnz].cpu().numpy()
+    vals_h = vals[:sample_nnz].cpu().numpy()
+    import oracle
+    F = [f.numpy() for f in synth.make_factors(spec.dims, R, seed=synth.factor_seed(
+        WORKLOAD_INDEX[args.workload]))]
+    N = len(spec.dims)
+
+    def step():
+        for n in range(N):
+            oracle.mttkrp(coo_h, vals_h, spec.dims, F, n)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    ms_full = dt * 1e3 * nnz_full / coo_h.shape[0]
+    line = {
+        "impl": "reference", "metric": "all-mode spMTTKRP ms per sweep", "value": ms_full,
+        "unit": "ms", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_full, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": spec.name, "rank": R, "nnz": nnz_full},
+        "cpu_baseline": {"value": ms_full, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"first {coo_h.shape[0]} nonzeros (draw order) of the workload, "
+                                   f"all {N} modes per step, time scaled by nnz"},
+        "e2e": {"value": ms_full, "unit": "ms", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    from paper_2405_08470_gb300 import Plan, _build
+    _build.build()
+    dev = torch.device("cuda")
+    spec, coo, vals = workload_tensors(args.workload, args.nnz, dev)
+    N = len(spec.dims)
+    R = args.rank or spec.ranks[0]
+    nnz = int(coo.shape[0])
+    s = 2 if args.dtype == "bf16" else 4
+    tdt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
+    fseed = synth.factor_seed(WORKLOAD_INDEX[args.workload])
+    F = [f.to(tdt) for f in synth.make_factors(spec.dims, R, seed=fseed, device=dev)]
+    touched = [int(torch.unique(coo[:, k]).numel()) for k in range(N)]
+    coo_h = coo.cpu().numpy()
+    vals_h = vals.cpu().numpy()
+    del coo, vals
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    plan = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, nblk=args.nblk, tile=args.tile)
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    outs = [torch.empty(d, R, device=dev) for d in spec.dims]
+    stream = torch.cuda.current_stream()
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        plan.sweep(F, outs)
+    torch.cuda.synchronize()
+
+    # timed region: K sweeps, CUDA events around every mode's launches
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(N + 1)] for _ in range(K)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.4)
+    barrier(world)
+    torch.cuda.synchronize()
+    start_mode = info["cur_mode"]
+    for i in range(K):
+        ev[i][0].record(stream)
+        for j in range(N):
+            n = (start_mode + j) % N
+            plan.compute(n, F, outs[n])
+            ev[i][j + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    per_mode = np.zeros(N)
+    total = 0.0
+    for i in range(K):
+        total += ev[i][0].elapsed_time(ev[i][N])
+        for j in range(N):
+            per_mode[(start_mode + j) % N] += ev[i][j].elapsed_time(ev[i][j + 1])
+    ms = total / K
+    per_mode /= K
+    ms = max_over_ranks(ms, world)
+
+    peak, peak_kind = load_peaks()
+    byts = compulsory_bytes(spec.dims, nnz, R, s, touched, N)
+    t_roof_ms = sum(byts) / (peak * 1e9) * 1e3
+    achieved = sum(byts) / (per_mode.sum() * 1e-3) / 1e9
+    traffic = ncu_traffic(args.workload, R, args.dtype)
+
+    # end to end through the public API with host buffers: H2D factors, sweep, D2H outputs
+    e2e = None
+    if not args.no_e2e:
+        Fh = [f.cpu().pin_memory() for f in F]
+        Oh = [torch.empty(d, R, pin_memory=True) for d in spec.dims]
+        Fd = [torch.empty_like(f, device=dev) for f in Fh]
+        h2d = sum(f.numel() * f.element_size() for f in Fh)
+        d2h = sum(o.numel() * o.element_size() for o in Oh)
+        for _ in range(2):
+            for a, b in zip(Fd, Fh):
+                a.copy_(b, non_blocking=True)
+            plan.sweep(Fd, outs, graph=True)
+            for a, b in zip(Oh, outs):
+                a.copy_(b, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        e0.record(stream)
+        for _ in range(K):
+            for a, b in zip(Fd, Fh):
+                a.copy_(b, non_blocking=True)
+            plan.sweep(Fd, outs, graph=True)
+            for a, b in zip(Oh, outs):
+                a.copy_(b, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / K, world)
+        e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        S, dt = cpu_oracle_sample(coo_h, vals_h, spec.dims, R, args.cpu_seconds, fseed)
+        cpu = {"value": dt * 1e3 * nnz / S, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"first {S} nonzeros (draw order) of the workload, all {N} modes, "
+                         f"FP64 numpy oracle, time scaled by nnz/{S}"}
+
+    launches = info["launches_per_sweep"] * K
+    if rank == 0:
+        line = {
+            "metric": "all-mode spMTTKRP ms per sweep", "value": ms, "unit": "ms",
+            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": spec.name, "dims": list(spec.dims), "nnz": nnz, "rank": R,
+                       "factor_dtype": args.dtype, "nblk": info["nblk"], "tile": info["tile"],
+                       "l2": "inputs larger than L2 (element stream "
+                             f"{nnz * info['elem_bytes'] / 1e9:.2f} GB per mode)",
+                       "parallelism": f"replicas x{world}"},
+            "pct_hbm_roofline": t_roof_ms / ms,
+            "t_roof_ms": t_roof_ms,
+            "per_mode_ms": per_mode.tolist(),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                         "kernel": "mttkrp_remap_kernel (+ splitrow_fixup, per-mode events)",
+                         "algorithmic_bytes_per_sweep": int(sum(byts))},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "plan_seconds": plan_s,
+            "touched_rows": touched,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

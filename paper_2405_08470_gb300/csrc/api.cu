@@ -311,6 +311,7 @@ int spmttkrp_plan_destroy(spmttkrp_plan_t p) {
   dfree(p->d_red);
   dfree(p->d_scal);
   dfree(p->d_vinv);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   p->destroyed = true;
   delete p;
   return SPM_OK;
@@ -366,7 +367,6 @@ int spmttkrp_sweep(spmttkrp_plan_t p, const void* const* factors, float* const* 
   for (int k = 0; k < p->N; ++k) key.push_back(factors[k]);
   for (int k = 0; k < p->N; ++k) key.push_back(outs[k]);
   key.push_back((const void*)(intptr_t)(p->cur_buf * 64 + p->cur_mode));
-  key.push_back((const void*)p->stream);
   GraphCache* hit = nullptr;
   for (auto& g : p->sweep_graphs)
     if (g.key == key) hit = &g;
@@ -379,9 +379,18 @@ int spmttkrp_sweep(spmttkrp_plan_t p, const void* const* factors, float* const* 
     p->cur_buf = buf0;
     p->cur_mode = mode0;
     cudaGraph_t g = nullptr;
-    SPM_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    // capture on an internal stream (the legacy default stream cannot capture)
+    if (!p->cap_stream) SPM_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = p->stream;
+    p->stream = p->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      p->stream = user;
+      return cuda_fail(e, "cudaStreamBeginCapture(sweep)");
+    }
     st = sweep_eager(p, factors, outs);
-    cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    e = cudaStreamEndCapture(p->stream, &g);
+    p->stream = user;
     p->cur_buf = buf1;
     p->cur_mode = mode1;
     if (st) {

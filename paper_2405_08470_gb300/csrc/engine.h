@@ -64,11 +64,13 @@ struct spmttkrp_plan {
   std::vector<int64_t> dims;
   size_t max_bytes = 0, dev_bytes = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // internal stream used only for graph capture
   int device = 0;
   int num_sms = 148;
 
-  // host copies kept for re-partitioning (row starts per mode) and queries
-  std::vector<std::vector<int64_t>> row_start;   // N x (dims[n] + 1)
+  // host copies kept for re-partitioning and queries: row_start[n] = starts of
+  // the nonempty rows of mode n (+ nnz), row_start[N + n] = their row ids
+  std::vector<std::vector<int64_t>> row_start;
   std::vector<std::vector<int32_t>> h_next_pos;  // host-only plans keep these
   std::vector<spm::ModeHost> mh;                 // per mode
   std::vector<uint8_t> h_elems;                  // host-only plans: mode-0 working copy
