@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--nnz", type=int, default=0, help="override nonzero count (small runs)")
     ap.add_argument("--nblk", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0, help="0 direct runs, 1 staged tiles")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -168,7 +169,7 @@ def kernel_digest():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2405_08470_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.startswith("mttkrp_kernel") or f.startswith("kernels_"):
+        if f.startswith("mttkrp_") or f.startswith("kernels_"):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -274,7 +275,8 @@ def main():
     del coo, vals
     torch.cuda.empty_cache()
     t0 = time.perf_counter()
-    plan = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, nblk=args.nblk, tile=args.tile)
+    plan = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, nblk=args.nblk, tile=args.tile,
+                variant=args.variant)
     plan_s = time.perf_counter() - t0
     info = plan.info()
     outs = [torch.empty(d, R, device=dev) for d in spec.dims]
@@ -365,6 +367,7 @@ def main():
             "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": spec.name, "dims": list(spec.dims), "nnz": nnz, "rank": R,
                        "factor_dtype": args.dtype, "nblk": info["nblk"], "tile": info["tile"],
+                       "kernel_form": ["direct runs", "staged tiles"][args.variant],
                        "l2": "inputs larger than L2 (element stream "
                              f"{nnz * info['elem_bytes'] / 1e9:.2f} GB per mode)",
                        "parallelism": f"replicas x{world}"},

@@ -65,6 +65,9 @@ typedef struct {
                        compute call (slow; for debugging)                         */
   int host_only;    /* 1 = build the plan on the host only (no device memory);
                        only spmttkrp_plan_query and destroy are then valid        */
+  int variant;      /* fused kernel form: 0 = each lane group streams one long
+                       contiguous run (default), 1 = tiles staged in shared memory
+                       by bulk async copies                                       */
   void* stream;     /* cudaStream_t for all work; NULL = default stream           */
 } spmttkrp_opts_t;
 
@@ -167,7 +170,8 @@ int cp_loss_bwd(spmttkrp_plan_t plan, const void* const* factors, const float* g
  * Chooses blocks per mode and tile size by timing all-mode sweeps with CUDA
  * events on the plan's own data, and applies the winner (deterministic
  * argmin of the median, ties to the first candidate).  Results are cached in
- * the JSON file named by $SPMTTKRP_TUNE_CACHE when set.
+ * the text file named by $SPMTTKRP_TUNE_CACHE when set (one line per key:
+ * "<shape key> <blocks per SM> <tile> <kernel form>").
  *   factors  host array of nmodes device pointers used for the trial sweeps.
  *   scratch  host array of nmodes device output buffers for the trial sweeps.
  *   flags    bit 0: ignore the cache.

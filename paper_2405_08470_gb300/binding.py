@@ -41,7 +41,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("factor_dtype", ctypes.c_int), ("partition", ctypes.c_int),
                 ("nblk", ctypes.c_int), ("tile", ctypes.c_int),
                 ("max_bytes", ctypes.c_size_t), ("checks", ctypes.c_int),
-                ("host_only", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("host_only", ctypes.c_int), ("variant", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -114,7 +115,7 @@ class Plan:
 
     def __init__(self, coo, vals, dims: Sequence[int], rank: int, dtype: str = "f32",
                  nblk: int = 0, tile: int = 0, max_bytes: int = 0, checks: bool = False,
-                 host_only: bool = False, stream=None):
+                 host_only: bool = False, stream=None, variant: int = 0):
         L = lib()
         coo = np.ascontiguousarray(np.asarray(coo.cpu() if hasattr(coo, "cpu") else coo,
                                               dtype=np.int64))
@@ -130,6 +131,7 @@ class Plan:
         o.factor_dtype = DTYPES[dtype]
         o.nblk, o.tile, o.max_bytes = int(nblk), int(tile), int(max_bytes)
         o.checks, o.host_only = int(bool(checks)), int(bool(host_only))
+        o.variant = int(variant)
         o.stream = None if host_only else _stream_ptr(stream)
         d = np.asarray(self.dims, dtype=np.int64)
         h = ctypes.c_void_p()

@@ -5,6 +5,7 @@
 #include <new>
 #include <string>
 
+#include "als.h"
 #include "engine.h"
 #include "mttkrp_kernel.cuh"
 
@@ -22,7 +23,7 @@ int cuda_fail(cudaError_t e, const char* what) {
   return SPM_ERR_CUDA;
 }
 
-static int dalloc(spmttkrp_plan* p, void** ptr, size_t bytes) {
+int plan_dalloc(spmttkrp_plan* p, void** ptr, size_t bytes) {
   bytes = std::max<size_t>(bytes, 16);
   if (p->max_bytes && p->dev_bytes + bytes > p->max_bytes)
     return fail(SPM_ERR_OOM, "plan device memory cap (max_bytes) exceeded");
@@ -57,9 +58,9 @@ int upload_mode_tables(spmttkrp_plan* p, int n) {
   d.nblk = h.nblk;
   d.nsplit = (int)h.splits.size();
   d.last_row = h.last_row;
-  int st = dalloc(p, (void**)&d.blkinfo, (size_t)d.nblk * sizeof(int4));
+  int st = plan_dalloc(p, (void**)&d.blkinfo, (size_t)d.nblk * sizeof(int4));
   if (st) return st;
-  st = dalloc(p, (void**)&d.splits, (size_t)d.nsplit * sizeof(SplitRow));
+  st = plan_dalloc(p, (void**)&d.splits, (size_t)d.nsplit * sizeof(SplitRow));
   if (st) return st;
   SPM_CUDA(cudaMemcpyAsync(d.blkinfo, h.blkinfo.data(), (size_t)d.nblk * sizeof(int4),
                            cudaMemcpyHostToDevice, p->stream));
@@ -74,7 +75,7 @@ int upload_mode_tables(spmttkrp_plan* p, int n) {
       p->dev_bytes -= std::max<size_t>(p->part_cap * 4, 16);
       p->d_part = nullptr;
     }
-    st = dalloc(p, (void**)&p->d_part, need * 4);
+    st = plan_dalloc(p, (void**)&p->d_part, need * 4);
     if (st) return st;
     p->part_cap = need;
   }
@@ -142,6 +143,7 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   a.err = p->d_err;
   a.scale = scale;
   a.dtype = p->dtype;
+  a.variant = p->variant;
   int st = launch_mttkrp(a, p->stream);
   if (st) return st;
   return launch_fixup(p->d_part, d.splits, d.nsplit, out, a.out_rows, p->R, scale, p->stream);
@@ -213,6 +215,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   if (o.tile != 0 && o.tile != 256 && o.tile != 512 && o.tile != 1024)
     return fail(SPM_ERR_INVALID_ARG, "tile must be 0, 256, 512 or 1024");
   if (o.nblk < 0) return fail(SPM_ERR_INVALID_ARG, "nblk must be >= 0");
+  if (o.variant != 0 && o.variant != 1) return fail(SPM_ERR_INVALID_ARG, "variant must be 0 or 1");
 
   spmttkrp_plan* p = new (std::nothrow) spmttkrp_plan();
   if (!p) return fail(SPM_ERR_OOM, "host allocation failed");
@@ -221,6 +224,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->nnz = nnz;
   p->dtype = o.factor_dtype;
   p->tile = o.tile ? o.tile : 512;
+  p->variant = o.variant;
   p->checks = o.checks;
   p->host_only = o.host_only;
   p->max_bytes = o.max_bytes;
@@ -253,9 +257,9 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     const int N = p->N;
     p->md.assign((size_t)N, ModeDev());
     const size_t eb = (size_t)p->nnz * p->es;
-    st = dalloc(p, (void**)&p->d_elem[0], eb);
-    if (!st) st = dalloc(p, (void**)&p->d_elem[1], eb);
-    if (!st) st = dalloc(p, (void**)&p->d_err, sizeof(int));
+    st = plan_dalloc(p, (void**)&p->d_elem[0], eb);
+    if (!st) st = plan_dalloc(p, (void**)&p->d_elem[1], eb);
+    if (!st) st = plan_dalloc(p, (void**)&p->d_err, sizeof(int));
     if (!st) {
       cudaError_t e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
       if (e == cudaSuccess && eb)
@@ -265,7 +269,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     }
     for (int n = 0; n < N && !st; ++n) {
       ModeDev& d = p->md[(size_t)n];
-      st = dalloc(p, (void**)&d.next_pos, ((size_t)p->nnz + 4) * sizeof(int32_t));
+      st = plan_dalloc(p, (void**)&d.next_pos, ((size_t)p->nnz + 4) * sizeof(int32_t));
       if (!st) {
         cudaError_t e = cudaMemsetAsync(d.next_pos, 0, ((size_t)p->nnz + 4) * 4, p->stream);
         if (e == cudaSuccess && p->nnz)
@@ -307,8 +311,11 @@ int spmttkrp_plan_destroy(spmttkrp_plan_t p) {
   dfree(p->d_part);
   dfree(p->d_err);
   dfree(p->d_M);
+  dfree(p->d_U);
   dfree(p->d_gram);
+  dfree(p->d_gpart);
   dfree(p->d_red);
+  dfree(p->d_chol);
   dfree(p->d_scal);
   dfree(p->d_vinv);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -451,6 +458,7 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
       o[13] = p->num_sms;
       std::memcpy(&o[14], &p->normx2, 8);
       o[15] = lane_config(p->R, p->dtype, true).L;
+      o[12] = p->host_only | (p->variant << 1);
       return SPM_OK;
     }
     case SPM_Q_NEXT_POS: {

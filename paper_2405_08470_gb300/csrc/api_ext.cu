@@ -1,21 +1,330 @@
-// api_ext.cu - CP-ALS, CP-loss and autotuning entry points (filled in below).
+// api_ext.cu - CP-ALS iteration (captured as a CUDA graph), CP loss forward /
+// backward, and the autotuner, on top of the fused spMTTKRP + remap path.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "als.h"
 #include "engine.h"
+#include "mttkrp_kernel.cuh"
+
+namespace spm {
+
+constexpr int kGramChunks = 256;
+
+static int ensure(spmttkrp_plan* p, void** ptr, size_t bytes) {
+  if (*ptr) return SPM_OK;
+  return plan_dalloc(p, ptr, bytes);
+}
+
+static int64_t max_dim(const spmttkrp_plan* p) {
+  int64_t m = 0;
+  for (int64_t d : p->dims) m = std::max(m, d);
+  return m;
+}
+
+static int ensure_als(spmttkrp_plan* p) {
+  const size_t R = (size_t)p->R, N = (size_t)p->N, I = (size_t)max_dim(p);
+  if (!p->red_nb) p->red_nb = std::max(1, p->num_sms * 2);
+  int st;
+  if ((st = ensure(p, (void**)&p->d_M, I * R * 4))) return st;
+  if ((st = ensure(p, (void**)&p->d_U, I * R * 4))) return st;
+  if ((st = ensure(p, (void**)&p->d_gram, N * R * R * 8))) return st;
+  if ((st = ensure(p, (void**)&p->d_gpart, (size_t)kGramChunks * R * R * 8))) return st;
+  if ((st = ensure(p, (void**)&p->d_red, (size_t)2 * p->red_nb * R * 8))) return st;
+  if ((st = ensure(p, (void**)&p->d_chol, 3 * R * R * 8))) return st;
+  if ((st = ensure(p, (void**)&p->d_vinv, R * R * 4))) return st;
+  if ((st = ensure(p, (void**)&p->d_scal, (8 + R) * 8))) return st;
+  return SPM_OK;
+}
+
+// Queues one CP-ALS iteration (modes 0..N-1) on p->stream.  The working copy
+// must be in mode-0 order; afterwards it is again.
+static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda) {
+  const int N = p->N, R = p->R;
+  int* status = reinterpret_cast<int*>(p->d_scal);
+  double* fit = p->d_scal + 1;
+  double* lam64 = p->d_scal + 8;
+  double* colsq = p->d_red;
+  double* mdot = p->d_red + (size_t)p->red_nb * R;
+  cudaStream_t s = p->stream;
+  SPM_CUDA(cudaMemsetAsync(p->d_scal, 0, 8, s));
+  int st;
+  for (int k = 0; k < N; ++k)
+    if ((st = launch_gram(factors[k], p->dtype, p->dims[(size_t)k], R, p->d_gpart, kGramChunks,
+                          p->d_gram + (size_t)k * R * R, s)))
+      return st;
+  std::vector<const void*> cf(factors, factors + N);
+  for (int n = 0; n < N; ++n) {
+    const int64_t I = p->dims[(size_t)n];
+    if ((st = compute_mode(p, n, cf.data(), p->d_M))) return st;
+    if ((st = launch_als_prep(p->d_gram, N, n, R, p->d_chol, p->d_vinv, status, s))) return st;
+    if ((st = launch_als_solve(p->d_M, p->d_U, p->d_vinv, I, R, colsq, status, p->red_nb, s)))
+      return st;
+    if ((st = launch_als_lambda(colsq, p->red_nb, R, lam64, lambda, status, s))) return st;
+    if ((st = launch_als_scale(p->d_U, p->d_M, factors[n], p->dtype, lam64, I, R, mdot, status,
+                               p->red_nb, s)))
+      return st;
+    if ((st = launch_gram(factors[n], p->dtype, I, R, p->d_gpart, kGramChunks,
+                          p->d_gram + (size_t)n * R * R, s)))
+      return st;
+  }
+  return launch_als_fit(p->d_gram, N, R, lam64, mdot, p->red_nb, p->normx2, fit, status, s);
+}
+
+static void drop_graphs(std::vector<GraphCache>& v) {
+  for (auto& g : v)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  v.clear();
+}
+
+// Re-cuts every mode into nblk blocks and switches the kernel form / tile.
+static int apply_config(spmttkrp_plan* p, int nblk, int tile, int variant) {
+  for (int n = 0; n < p->N; ++n) {
+    int st = partition_mode(p, n, nblk, &p->mh[(size_t)n]);
+    if (st) return st;
+    st = upload_mode_tables(p, n);
+    if (st) return st;
+  }
+  p->tile = tile;
+  p->variant = variant;
+  drop_graphs(p->sweep_graphs);
+  drop_graphs(p->als_graphs);
+  return SPM_OK;
+}
+
+// ---- autotune cache: one line per key, "key nblk_per_sm tile variant"
+static std::string tune_key(const spmttkrp_plan* p) {
+  int64_t maxdeg = 0;
+  for (int n = 0; n < p->N; ++n) {
+    const auto& us = p->row_start[(size_t)n];
+    for (size_t u = 0; u + 1 < us.size(); ++u) maxdeg = std::max(maxdeg, us[u + 1] - us[u]);
+  }
+  const int zbucket = p->nnz > 0 ? (int)std::floor(std::log2((double)p->nnz)) : 0;
+  const int skew = p->nnz > 0 ? (int)std::floor(20.0 * (double)maxdeg / (double)p->nnz) : 0;
+  std::ostringstream o;
+  o << "N" << p->N << "_R" << p->R << "_d" << p->dtype << "_z" << zbucket << "_s" << skew
+    << "_m" << p->num_sms;
+  return o.str();
+}
+
+static bool cache_lookup(const std::string& key, int* nps, int* tile, int* variant) {
+  const char* path = std::getenv("SPMTTKRP_TUNE_CACHE");
+  if (!path) return false;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    std::istringstream is(line);
+    std::string k;
+    int a, b, c;
+    if (is >> k >> a >> b >> c && k == key) {
+      *nps = a;
+      *tile = b;
+      *variant = c;
+      return true;
+    }
+  }
+  return false;
+}
+
+static void cache_store(const std::string& key, int nps, int tile, int variant) {
+  const char* path = std::getenv("SPMTTKRP_TUNE_CACHE");
+  if (!path) return;
+  std::vector<std::string> keep;
+  {
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+      std::istringstream is(line);
+      std::string k;
+      if (is >> k && k != key) keep.push_back(line);
+    }
+  }
+  std::ofstream f(path, std::ios::trunc);
+  for (auto& l : keep) f << l << "\n";
+  f << key << " " << nps << " " << tile << " " << variant << "\n";
+}
+
+}  // namespace spm
 
 using namespace spm;
 
 extern "C" {
 
-int cp_als_iter(spmttkrp_plan_t, void* const*, float*, double*) {
-  return fail(SPM_ERR_UNSUPPORTED, "cp_als_iter: not built yet");
+int cp_als_iter(spmttkrp_plan_t p, void* const* factors, float* lambda, double* fit) {
+  if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
+  if (p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
+  if (!factors || !lambda || !fit) return fail(SPM_ERR_INVALID_ARG, "null argument");
+  for (int k = 0; k < p->N; ++k)
+    if (!factors[k]) return fail(SPM_ERR_INVALID_ARG, "null factor pointer");
+  if (p->nnz == 0) return fail(SPM_ERR_INVALID_ARG, "CP-ALS needs at least one nonzero");
+  int st = ensure_als(p);
+  if (st) return st;
+  st = spmttkrp_remap(p, 0);
+  if (st) return st;
+  std::vector<const void*> key(factors, factors + p->N);
+  key.push_back(lambda);
+  key.push_back((const void*)(intptr_t)p->cur_buf);
+  GraphCache* hit = nullptr;
+  for (auto& g : p->als_graphs)
+    if (g.key == key) hit = &g;
+  if (hit) {
+    SPM_CUDA(cudaGraphLaunch(hit->exec, p->stream));
+    if (p->N & 1) p->cur_buf ^= 1;
+  } else {
+    const int buf0 = p->cur_buf;
+    st = als_enqueue(p, factors, lambda);  // eager first run
+    if (st) return st;
+    const int buf1 = p->cur_buf;
+    // capture the same sequence for later calls with these pointers
+    if (!p->cap_stream) SPM_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = p->stream;
+    p->stream = p->cap_stream;
+    p->cur_buf = buf0;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      st = als_enqueue(p, factors, lambda);
+      e = cudaStreamEndCapture(p->stream, &g);
+    }
+    p->stream = user;
+    p->cur_buf = buf1;
+    p->cur_mode = 0;
+    if (st) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "ALS graph capture");
+    GraphCache gc;
+    gc.key = key;
+    e = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(ALS)");
+    if (p->als_graphs.size() >= 4) {
+      cudaGraphExecDestroy(p->als_graphs.front().exec);
+      p->als_graphs.erase(p->als_graphs.begin());
+    }
+    p->als_graphs.push_back(gc);
+  }
+  p->cur_mode = 0;
+  double host[2] = {0.0, 0.0};
+  SPM_CUDA(cudaMemcpyAsync(host, p->d_scal, 16, cudaMemcpyDeviceToHost, p->stream));
+  SPM_CUDA(cudaStreamSynchronize(p->stream));
+  int status;
+  std::memcpy(&status, host, sizeof(int));
+  *fit = host[1];
+  if (status) return fail(SPM_ERR_NOT_SPD, "Hadamard product of Gram matrices is not SPD");
+  return SPM_OK;
 }
-int cp_loss_fwd(spmttkrp_plan_t, const void* const*, float*) {
-  return fail(SPM_ERR_UNSUPPORTED, "cp_loss_fwd: not built yet");
+
+int cp_loss_fwd(spmttkrp_plan_t p, const void* const* factors, float* loss) {
+  if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
+  if (p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
+  if (!factors || !loss) return fail(SPM_ERR_INVALID_ARG, "null argument");
+  for (int k = 0; k < p->N; ++k)
+    if (!factors[k]) return fail(SPM_ERR_INVALID_ARG, "null factor pointer");
+  int st = ensure_als(p);
+  if (st) return st;
+  if ((st = ensure(p, (void**)&p->d_elem[2], (size_t)p->nnz * p->es))) return st;
+  FactorPtrs fp;
+  for (int k = 0; k < p->N; ++k) fp.p[k] = factors[k];
+  st = launch_cp_fwd(p->d_elem[p->cur_buf], p->d_elem[2], p->nnz, p->es, p->N, fp, p->R,
+                     p->dtype, p->d_red, p->red_nb, loss, p->d_scal + 2, p->stream);
+  if (st) return st;
+  p->res_valid = 1;
+  p->res_mode = p->cur_mode;
+  return SPM_OK;
 }
-int cp_loss_bwd(spmttkrp_plan_t, const void* const*, const float*, float* const*) {
-  return fail(SPM_ERR_UNSUPPORTED, "cp_loss_bwd: not built yet");
+
+int cp_loss_bwd(spmttkrp_plan_t p, const void* const* factors, const float* grad_out,
+                float* const* grads) {
+  if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
+  if (p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
+  if (!factors || !grad_out || !grads) return fail(SPM_ERR_INVALID_ARG, "null argument");
+  for (int k = 0; k < p->N; ++k)
+    if (!factors[k] || !grads[k]) return fail(SPM_ERR_INVALID_ARG, "null factor or grad");
+  if (!p->res_valid) return fail(SPM_ERR_STATE, "cp_loss_bwd needs a preceding cp_loss_fwd");
+  // the residual copy ping-pongs between its own buffer and the free half of
+  // the working-copy pair; N fused passes bring it back to its start order
+  uint8_t* bufs[2] = {p->d_elem[2], p->d_elem[1 - p->cur_buf]};
+  int cur = 0;
+  for (int i = 0; i < p->N; ++i) {
+    const int n = (p->res_mode + i) % p->N;
+    int st = run_mode(p, n, factors, grads[n], bufs[cur], bufs[1 - cur], grad_out);
+    if (st) return st;
+    if (p->nnz > 0) cur ^= 1;
+  }
+  p->res_valid = 0;
+  return p->checks ? spmttkrp_device_status(p) : SPM_OK;
 }
-int spmttkrp_autotune(spmttkrp_plan_t, const void* const*, float* const*, int) {
-  return fail(SPM_ERR_UNSUPPORTED, "spmttkrp_autotune: not built yet");
+
+int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* const* scratch,
+                      int flags) {
+  if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
+  if (p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
+  if (!factors || !scratch) return fail(SPM_ERR_INVALID_ARG, "null argument");
+  if (p->nnz == 0) return SPM_OK;
+  const std::string key = tune_key(p);
+  int nps = 0, tile = 0, variant = 0;
+  if (!(flags & 1) && cache_lookup(key, &nps, &tile, &variant))
+    return apply_config(p, std::max(1, nps * p->num_sms), tile, variant);
+
+  struct Cand {
+    int nps, tile, variant;
+  };
+  std::vector<Cand> cands;
+  for (int v : {0, 1})
+    for (int n : {2, 4, 8, 16, 32, 64}) {
+      if (n > 4 && (int64_t)n * p->num_sms * 256 > p->nnz) continue;
+      if (v == 0) {
+        cands.push_back({n, p->tile, 0});
+      } else {
+        for (int t : {256, 512, 1024})
+          if (mttkrp_smem_bytes(p->es, t, p->R, p->dtype) <= 200 * 1024) cands.push_back({n, t, 1});
+      }
+    }
+  cudaEvent_t e0, e1;
+  SPM_CUDA(cudaEventCreate(&e0));
+  SPM_CUDA(cudaEventCreate(&e1));
+  double best = 1e300;
+  Cand win = cands.front();
+  int st = SPM_OK;
+  for (const Cand& c : cands) {
+    st = apply_config(p, std::max(1, c.nps * p->num_sms), c.tile, c.variant);
+    if (st) break;
+    st = spmttkrp_sweep(p, factors, scratch, 0);  // warm
+    if (st) break;
+    std::vector<float> ms;
+    for (int rep = 0; rep < 3 && !st; ++rep) {
+      cudaEventRecord(e0, p->stream);
+      st = spmttkrp_sweep(p, factors, scratch, 0);
+      cudaEventRecord(e1, p->stream);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms.push_back(t);
+    }
+    if (st) break;
+    std::sort(ms.begin(), ms.end());
+    if (ms[1] < best) {
+      best = ms[1];
+      win = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  st = apply_config(p, std::max(1, win.nps * p->num_sms), win.tile, win.variant);
+  if (st) return st;
+  cache_store(key, win.nps, win.tile, win.variant);
+  return SPM_OK;
 }
 
 }  // extern "C"

@@ -59,6 +59,7 @@ struct GraphCache {
 
 struct spmttkrp_plan {
   int N = 0, R = 0, dtype = 0, tile = 512, checks = 0, host_only = 0;
+  int variant = 0;  // fused-kernel form: 0 = direct runs, 1 = staged tiles
   int64_t nnz = 0;
   int es = 16;  // element stride in bytes: {int32 idx[N]; float val}, rounded up to 16
   std::vector<int64_t> dims;
@@ -84,16 +85,18 @@ struct spmttkrp_plan {
   float* d_part = nullptr;   // split-row partials: max nblk x 2 x R
   size_t part_cap = 0;       // floats
   int* d_err = nullptr;      // device error word
-  // ALS / CP-loss scratch
-  float* d_M = nullptr;      // max_n dims[n] x R
-  double* d_gram = nullptr;  // N x R x R
-  double* d_red = nullptr;   // reduction partials
-  size_t red_cap = 0;
-  double* d_scal = nullptr;  // small FP64 scalars (loss, fit terms)
-  float* d_vinv = nullptr;   // R x R
-  int res_valid = 0;         // residual copy d_elem[2] is current
-  int res_mode = 0;          // order the residual copy is in
-  int res_buf = 2;           // which buffer holds the residual copy (2 or the free one)
+  // ALS / CP-loss scratch (allocated on first use)
+  float* d_M = nullptr;       // max_n dims[n] x R: spMTTKRP output of the ALS mode
+  float* d_U = nullptr;       // max_n dims[n] x R: M V^-1 before normalisation
+  double* d_gram = nullptr;   // N x R x R Gram matrices
+  double* d_gpart = nullptr;  // kGramChunks x R x R Gram partials
+  double* d_red = nullptr;    // 2 x red_nb x R reduction partials
+  int red_nb = 0;             // blocks of the row-wise ALS kernels (fixed per plan)
+  double* d_chol = nullptr;   // 3 x R x R FP64 Cholesky work
+  double* d_scal = nullptr;   // [0] status (as int), [1] fit, [2] loss, [8..8+R) lambda
+  float* d_vinv = nullptr;    // R x R
+  int res_valid = 0;          // residual copy d_elem[2] is current (after cp_loss_fwd)
+  int res_mode = 0;           // order the residual copy is in
   std::vector<spm::GraphCache> sweep_graphs;  // by parity
   std::vector<spm::GraphCache> als_graphs;
   bool destroyed = false;
@@ -131,6 +134,7 @@ struct MttkrpArgs {
   int* err;
   const float* scale;      // device scalar multiplier or null
   int dtype;
+  int variant;             // 0 = direct runs, 1 = staged tiles
 };
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
 int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* out,

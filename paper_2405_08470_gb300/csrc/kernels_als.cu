@@ -1,0 +1,390 @@
+// kernels_als.cu - the CP-ALS update around the fused spMTTKRP (Section 2.1.3;
+// the update itself is Kolda-Bader's CP-ALS, which the paper cites):
+//   G_k = A_k^T A_k            FP32 per-chunk partials, FP64 fixed-order sum
+//   V   = Hadamard_{k!=n} G_k  FP64, Cholesky V = L L^T and V^-1 in FP64
+//   U   = M_n V^-1             FP32 (V^-1 stored as FP32), column norms^2
+//   lambda = sqrt(sum_i U^2)   FP64 fixed-order sum
+//   A_n = U / lambda           stored as the factor type (FP32 or BF16)
+//   fit from |X|^2, lambda, the G_k and <X, Y> (last mode).
+// Every reduction runs in a fixed order over a fixed grid, so the results are
+// bit-identical from run to run.  A failed Cholesky sets a device status word
+// that makes the remaining update kernels of the iteration return at once.
+#include <cuda_bf16.h>
+
+#include "engine.h"
+#include "als.h"
+
+namespace spm {
+
+template <typename T>
+__device__ __forceinline__ float to_f(T x);
+template <>
+__device__ __forceinline__ float to_f<float>(float x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) {
+  return __bfloat162float(x);
+}
+template <typename T>
+__device__ __forceinline__ T from_f(float x);
+template <>
+__device__ __forceinline__ float from_f<float>(float x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+
+// ---- Gram partials: block (chunk, rt, st) computes G[rt*32.., st*32..] over its rows
+template <typename T>
+__global__ void __launch_bounds__(256) gram_partial_kernel(const T* __restrict__ A, int64_t I,
+                                                           int R, int64_t rows_per_chunk,
+                                                           double* __restrict__ part) {
+  __shared__ float Ar[64][33];
+  __shared__ float As[64][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int chunk = blockIdx.x, r0 = blockIdx.y * 32, s0 = blockIdx.z * 32;
+  const int64_t lo = (int64_t)chunk * rows_per_chunk;
+  const int64_t hi = min(I, lo + rows_per_chunk);
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int64_t base = lo; base < hi; base += 64) {
+    for (int q = threadIdx.x; q < 64 * 32; q += 256) {
+      const int rr = q >> 5, cc = q & 31;
+      const int64_t row = base + rr;
+      const bool ok = row < hi;
+      Ar[rr][cc] = (ok && r0 + cc < R) ? to_f<T>(A[row * R + r0 + cc]) : 0.f;
+      As[rr][cc] = (ok && s0 + cc < R) ? to_f<T>(A[row * R + s0 + cc]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < 64; ++q) {
+      const float a = Ar[q][tx];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] += a * As[q][ty + 8 * j];
+    }
+    __syncthreads();
+  }
+  for (int j = 0; j < 4; ++j) {
+    const int r = r0 + tx, s = s0 + ty + 8 * j;
+    if (r < R && s < R) part[((size_t)chunk * R + r) * R + s] = (double)acc[j];
+  }
+}
+
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int nchunk, int R,
+                                   double* __restrict__ G) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= R * R) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * R * R + q];
+  G[q] = s;
+}
+
+// ---- V = Hadamard of the other Grams, Cholesky, V^-1 (one block, FP64)
+__global__ void __launch_bounds__(256) als_prep_kernel(const double* __restrict__ grams, int N,
+                                                       int n, int R, double* __restrict__ work,
+                                                       float* __restrict__ vinv,
+                                                       int* __restrict__ status) {
+  double* V = work;
+  double* L = work + (size_t)R * R;
+  double* Li = work + (size_t)2 * R * R;
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = *status;
+  __syncthreads();
+  if (bad) return;
+  for (int q = tid; q < R * R; q += blockDim.x) {
+    double v = 1.0;
+    for (int k = 0; k < N; ++k)
+      if (k != n) v *= grams[(size_t)k * R * R + q];
+    V[q] = v;
+    L[q] = 0.0;
+    Li[q] = 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < R; ++j) {
+    if (tid == 0) {
+      double d = V[(size_t)j * R + j];
+      for (int k = 0; k < j; ++k) d -= L[(size_t)j * R + k] * L[(size_t)j * R + k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+      } else {
+        L[(size_t)j * R + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double ljj = L[(size_t)j * R + j];
+    for (int i = j + 1 + tid; i < R; i += blockDim.x) {
+      double s = V[(size_t)i * R + j];
+      for (int k = 0; k < j; ++k) s -= L[(size_t)i * R + k] * L[(size_t)j * R + k];
+      L[(size_t)i * R + j] = s / ljj;
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0) *status = SPM_ERR_NOT_SPD;
+    return;
+  }
+  // L^-1 column by column (lower triangular)
+  for (int c = tid; c < R; c += blockDim.x) {
+    Li[(size_t)c * R + c] = 1.0 / L[(size_t)c * R + c];
+    for (int i = c + 1; i < R; ++i) {
+      double s = 0.0;
+      for (int k = c; k < i; ++k) s += L[(size_t)i * R + k] * Li[(size_t)k * R + c];
+      Li[(size_t)i * R + c] = -s / L[(size_t)i * R + i];
+    }
+  }
+  __syncthreads();
+  // V^-1 = L^-T L^-1
+  for (int q = tid; q < R * R; q += blockDim.x) {
+    const int i = q / R, j = q % R;
+    double s = 0.0;
+    for (int k = max(i, j); k < R; ++k) s += Li[(size_t)k * R + i] * Li[(size_t)k * R + j];
+    vinv[q] = (float)s;
+  }
+}
+
+// ---- U = M V^-1 (warp per row), per-block column sums of U^2
+template <int CC>
+__global__ void __launch_bounds__(256) als_solve_kernel(const float* __restrict__ M,
+                                                        float* __restrict__ U,
+                                                        const float* __restrict__ vinv, int64_t I,
+                                                        int R, double* __restrict__ colsq_part,
+                                                        const int* __restrict__ status) {
+  extern __shared__ float vs[];  // R x R when R <= 128, else unused
+  __shared__ float wsum[8][CC * 32];
+  if (*status) return;
+  const bool in_smem = R <= 128;
+  if (in_smem)
+    for (int q = threadIdx.x; q < R * R; q += 256) vs[q] = vinv[q];
+  __syncthreads();
+  const float* V = in_smem ? vs : vinv;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float csq[CC];
+#pragma unroll
+  for (int c = 0; c < CC; ++c) csq[c] = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * 8;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < I; i += stride) {
+    float m[CC], u[CC];
+#pragma unroll
+    for (int c = 0; c < CC; ++c) {
+      const int r = lane + 32 * c;
+      m[c] = r < R ? M[i * R + r] : 0.f;
+      u[c] = 0.f;
+    }
+#pragma unroll
+    for (int cj = 0; cj < CC; ++cj) {
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = cj * 32 + jj;
+        const float mj = __shfl_sync(0xffffffffu, m[cj], jj);
+        if (j < R) {
+#pragma unroll
+          for (int c = 0; c < CC; ++c) {
+            const int r = lane + 32 * c;
+            if (r < R) u[c] = fmaf(mj, V[(size_t)j * R + r], u[c]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CC; ++c) {
+      const int r = lane + 32 * c;
+      if (r < R) {
+        U[i * R + r] = u[c];
+        csq[c] = fmaf(u[c], u[c], csq[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CC; ++c) wsum[w][lane + 32 * c] = csq[c];
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += 256) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += (double)wsum[q][r];
+    colsq_part[(size_t)blockIdx.x * R + r] = s;
+  }
+}
+
+__global__ void als_lambda_kernel(const double* __restrict__ colsq_part, int nb, int R,
+                                  double* __restrict__ lam64, float* __restrict__ lam_out,
+                                  const int* __restrict__ status) {
+  if (*status) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += colsq_part[(size_t)b * R + r];
+  const double l = sqrt(s);
+  lam64[r] = l;
+  lam_out[r] = (float)l;
+}
+
+// ---- A_n = U / lambda (stored as T); per-block sums of M * A_n (for <X, Y>)
+template <typename T, int CC>
+__global__ void __launch_bounds__(256) als_scale_kernel(const float* __restrict__ U,
+                                                        const float* __restrict__ M,
+                                                        T* __restrict__ A,
+                                                        const double* __restrict__ lam64,
+                                                        int64_t I, int R,
+                                                        double* __restrict__ mdot_part,
+                                                        const int* __restrict__ status) {
+  __shared__ float wsum[8][CC * 32];
+  if (*status) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float inv[CC], md[CC];
+#pragma unroll
+  for (int c = 0; c < CC; ++c) {
+    const int r = lane + 32 * c;
+    inv[c] = r < R ? (float)(1.0 / lam64[r]) : 0.f;
+    md[c] = 0.f;
+  }
+  const int64_t stride = (int64_t)gridDim.x * 8;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < I; i += stride) {
+#pragma unroll
+    for (int c = 0; c < CC; ++c) {
+      const int r = lane + 32 * c;
+      if (r < R) {
+        const T a = from_f<T>(U[i * R + r] * inv[c]);
+        A[i * R + r] = a;
+        md[c] = fmaf(M[i * R + r], to_f<T>(a), md[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CC; ++c) wsum[w][lane + 32 * c] = md[c];
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += 256) {
+    double s = 0.0;
+    for (int q = 0; q < 8; ++q) s += (double)wsum[q][r];
+    mdot_part[(size_t)blockIdx.x * R + r] = s;
+  }
+}
+
+// ---- fit = 1 - sqrt(|X|^2 + |Y|^2 - 2 <X,Y>) / |X|
+__global__ void __launch_bounds__(256) als_fit_kernel(const double* __restrict__ grams, int N,
+                                                      int R, const double* __restrict__ lam64,
+                                                      const double* __restrict__ mdot_part,
+                                                      int nb, double normx2,
+                                                      double* __restrict__ fit_out,
+                                                      const int* __restrict__ status) {
+  __shared__ double red[256];
+  __shared__ double red2[256];
+  const int tid = threadIdx.x;
+  double y2 = 0.0, xy = 0.0;
+  for (int q = tid; q < R * R; q += 256) {
+    const int r = q / R, s = q % R;
+    double h = 1.0;
+    for (int k = 0; k < N; ++k) h *= grams[(size_t)k * R * R + q];
+    y2 += lam64[r] * lam64[s] * h;
+  }
+  for (int r = tid; r < R; r += 256) {
+    double m = 0.0;
+    for (int b = 0; b < nb; ++b) m += mdot_part[(size_t)b * R + r];
+    xy += lam64[r] * m;
+  }
+  red[tid] = y2;
+  red2[tid] = xy;
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < 256; ++q) {
+      a += red[q];
+      b += red2[q];
+    }
+    const double res2 = fmax(normx2 + a - 2.0 * b, 0.0);
+    fit_out[0] = *status ? nan("") : 1.0 - sqrt(res2) / sqrt(normx2);
+  }
+}
+
+// ------------------------------------------------------------ launchers
+
+int launch_gram(const void* A, int dtype, int64_t I, int R, double* part, int max_chunks,
+                double* G, cudaStream_t s) {
+  int64_t rpc = std::max<int64_t>(2048, (I + max_chunks - 1) / max_chunks);
+  int nchunk = (int)std::max<int64_t>(1, (I + rpc - 1) / rpc);
+  const int nt = (R + 31) / 32;
+  dim3 grid(nchunk, nt, nt);
+  if (dtype == SPM_DTYPE_BF16)
+    gram_partial_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(
+        static_cast<const __nv_bfloat16*>(A), I, R, rpc, part);
+  else
+    gram_partial_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float*>(A), I, R, rpc,
+                                                    part);
+  gram_reduce_kernel<<<(R * R + 255) / 256, 256, 0, s>>>(part, nchunk, R, G);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "gram kernels");
+}
+
+int launch_als_prep(const double* grams, int N, int n, int R, double* work, float* vinv,
+                    int* status, cudaStream_t s) {
+  als_prep_kernel<<<1, 256, 0, s>>>(grams, N, n, R, work, vinv, status);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "als_prep_kernel");
+}
+
+template <int CC>
+static int solve_cc(const float* M, float* U, const float* vinv, int64_t I, int R,
+                    double* colsq, const int* status, int nb, cudaStream_t s) {
+  const size_t smem = R <= 128 ? (size_t)R * R * 4 : 0;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(als_solve_kernel<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         128 * 128 * 4);
+    configured = true;
+  }
+  als_solve_kernel<CC><<<nb, 256, smem, s>>>(M, U, vinv, I, R, colsq, status);
+  return SPM_OK;
+}
+
+int launch_als_solve(const float* M, float* U, const float* vinv, int64_t I, int R,
+                     double* colsq, const int* status, int nb, cudaStream_t s) {
+  const int cc = (R + 31) / 32;
+  if (cc <= 1) solve_cc<1>(M, U, vinv, I, R, colsq, status, nb, s);
+  else if (cc <= 2) solve_cc<2>(M, U, vinv, I, R, colsq, status, nb, s);
+  else if (cc <= 4) solve_cc<4>(M, U, vinv, I, R, colsq, status, nb, s);
+  else solve_cc<8>(M, U, vinv, I, R, colsq, status, nb, s);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "als_solve_kernel");
+}
+
+int launch_als_lambda(const double* colsq, int nb, int R, double* lam64, float* lam_out,
+                      const int* status, cudaStream_t s) {
+  als_lambda_kernel<<<(R + 255) / 256, 256, 0, s>>>(colsq, nb, R, lam64, lam_out, status);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "als_lambda_kernel");
+}
+
+template <typename T, int CC>
+static void scale_cc(const float* U, const float* M, void* A, const double* lam64, int64_t I,
+                     int R, double* mdot, const int* status, int nb, cudaStream_t s) {
+  als_scale_kernel<T, CC><<<nb, 256, 0, s>>>(U, M, static_cast<T*>(A), lam64, I, R, mdot,
+                                             status);
+}
+
+int launch_als_scale(const float* U, const float* M, void* A, int dtype, const double* lam64,
+                     int64_t I, int R, double* mdot, const int* status, int nb, cudaStream_t s) {
+  const int cc = (R + 31) / 32;
+  if (dtype == SPM_DTYPE_BF16) {
+    if (cc <= 1) scale_cc<__nv_bfloat16, 1>(U, M, A, lam64, I, R, mdot, status, nb, s);
+    else if (cc <= 2) scale_cc<__nv_bfloat16, 2>(U, M, A, lam64, I, R, mdot, status, nb, s);
+    else if (cc <= 4) scale_cc<__nv_bfloat16, 4>(U, M, A, lam64, I, R, mdot, status, nb, s);
+    else scale_cc<__nv_bfloat16, 8>(U, M, A, lam64, I, R, mdot, status, nb, s);
+  } else {
+    if (cc <= 1) scale_cc<float, 1>(U, M, A, lam64, I, R, mdot, status, nb, s);
+    else if (cc <= 2) scale_cc<float, 2>(U, M, A, lam64, I, R, mdot, status, nb, s);
+    else if (cc <= 4) scale_cc<float, 4>(U, M, A, lam64, I, R, mdot, status, nb, s);
+    else scale_cc<float, 8>(U, M, A, lam64, I, R, mdot, status, nb, s);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "als_scale_kernel");
+}
+
+int launch_als_fit(const double* grams, int N, int R, const double* lam64, const double* mdot,
+                   int nb, double normx2, double* fit_out, const int* status, cudaStream_t s) {
+  als_fit_kernel<<<1, 256, 0, s>>>(grams, N, R, lam64, mdot, nb, normx2, fit_out, status);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "als_fit_kernel");
+}
+
+}  // namespace spm

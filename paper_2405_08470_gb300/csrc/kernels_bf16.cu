@@ -1,10 +1,30 @@
 // kernels_bf16.cu - BF16-factor instantiations of the fused spMTTKRP + remap
 // kernel (factor rows stored in BF16, products and sums in FP32).
+#include "mttkrp_direct.cuh"
 #include "mttkrp_kernel.cuh"
 
 namespace spm {
 
+static int launch_direct_bfloat16(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
+  if (c.vec) {
+    switch (a.nmodes) {
+      case 3: return launch_direct<3, __nv_bfloat16, 8, 1, 4>(a, c.L, s);
+      case 4: return launch_direct<4, __nv_bfloat16, 8, 1, 4>(a, c.L, s);
+      case 5: return launch_direct<5, __nv_bfloat16, 8, 1, 4>(a, c.L, s);
+      case 6: return launch_direct<6, __nv_bfloat16, 8, 1, 4>(a, c.L, s);
+      default: return launch_direct<0, __nv_bfloat16, 8, 1, 2>(a, c.L, s);
+    }
+  }
+  switch (c.RC) {
+    case 1: return launch_direct<0, __nv_bfloat16, 1, 1, 2>(a, c.L, s);
+    case 2: return launch_direct<0, __nv_bfloat16, 1, 2, 2>(a, c.L, s);
+    case 4: return launch_direct<0, __nv_bfloat16, 1, 4, 2>(a, c.L, s);
+    default: return launch_direct<0, __nv_bfloat16, 1, 8, 2>(a, c.L, s);
+  }
+}
+
 int launch_mttkrp_bf16(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
+  if (a.variant == 0) return launch_direct_bfloat16(a, c, s);
   if (c.vec) {
     switch (a.nmodes) {
       case 3: return launch_variant<3, __nv_bfloat16, 8, 1>(a, c.L, s);

@@ -1,0 +1,135 @@
+// kernels_cploss.cu - CP loss on the observed entries (completion form):
+//   m_e = sum_r prod_k A_k[i_k(e), r],   e_e = m_e - x_e,   L = 1/2 sum_e e_e^2.
+// One pass over the working copy in whatever mode order it is in: groups of L
+// lanes own one nonzero at a time (16-byte factor-row slices per lane, as in
+// the spMTTKRP kernel), the model value is summed across the group with
+// shuffles, and the nonzero is written to the residual copy with its value
+// replaced by e_e.  The gradient is then one all-mode spMTTKRP sweep of the
+// residual copy.  The loss is reduced in a fixed order (FP64).
+#include "als.h"
+#include "mttkrp_kernel.cuh"
+
+namespace spm {
+
+template <int NT, typename T, int VW, int RC>
+__global__ void __launch_bounds__(256) cp_fwd_kernel(const uint8_t* __restrict__ elems,
+                                                     uint8_t* __restrict__ res, int64_t nnz,
+                                                     int es, int nmodes, FactorPtrs fp, int R,
+                                                     int L, double* __restrict__ loss_part) {
+  constexpr int NV = VW * RC;
+  const int N = NT > 0 ? NT : nmodes;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int sub = lane % L, gw = lane / L, G = 32 / L;
+  const int64_t gid = ((int64_t)blockIdx.x * 8 + w) * G + gw;
+  const int64_t ngroups = (int64_t)gridDim.x * 8 * G;
+  double sq = 0.0;
+  // the loop bound is uniform across the warp so that the shuffles below see
+  // every lane; groups past the end carry an inactive flag
+  for (int64_t eb = gid - gw; eb < nnz; eb += ngroups) {
+    const int64_t e = eb + gw;
+    const bool active = e < nnz;
+    const int* el = reinterpret_cast<const int*>(elems + (active ? e : 0) * es);
+    float p[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) p[j] = active ? 1.f : 0.f;
+    for (int k = 0; k < N && active; ++k) {
+      const int64_t idx = __ldg(el + k);
+      float x[NV];
+      if constexpr (VW > 1) {
+        if (sub * VW < R) {
+          Slice<T, VW>::load(fp.p[k], idx, R, sub, x);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NV; ++j) x[j] = 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+          const int r = sub + L * j;
+          x[j] = r < R ? load_scalar<T>(fp.p[k], idx * R + r) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NV; ++j) p[j] *= x[j];
+    }
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) m += p[j];
+    for (int off = L / 2; off > 0; off >>= 1) m += __shfl_xor_sync(0xffffffffu, m, off);
+    if (active && sub == 0) {
+      const float x = __int_as_float(__ldg(el + N));
+      const float r = m - x;
+      sq += (double)r * (double)r;
+      const int nv = es / 16;
+      const uint4* src = reinterpret_cast<const uint4*>(el);
+      uint4* dst = reinterpret_cast<uint4*>(res + e * es);
+      for (int c = 0; c < nv; ++c) {
+        uint4 v = __ldg(src + c);
+        const int word = N - 4 * c;  // value field: int index N of the element
+        if (word == 0) v.x = __float_as_uint(r);
+        else if (word == 1) v.y = __float_as_uint(r);
+        else if (word == 2) v.z = __float_as_uint(r);
+        else if (word == 3) v.w = __float_as_uint(r);
+        dst[c] = v;
+      }
+    }
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < 256; ++q) s += red[q];
+    loss_part[blockIdx.x] = s;
+  }
+}
+
+__global__ void cp_loss_final_kernel(const double* __restrict__ part, int nb,
+                                     float* __restrict__ loss, double* __restrict__ loss64) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[b];
+  loss64[0] = 0.5 * s;
+  loss[0] = (float)(0.5 * s);
+}
+
+template <typename T>
+static int fwd_dispatch(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N,
+                        const FactorPtrs& fp, int R, bool aligned, double* part, int nb,
+                        cudaStream_t s) {
+  const int dtype = std::is_same<T, float>::value ? SPM_DTYPE_F32 : SPM_DTYPE_BF16;
+  const LaneCfg c = lane_config(R, dtype, aligned);
+  constexpr int VWV = std::is_same<T, float>::value ? 4 : 8;
+  if (c.vec) {
+    if (N == 3)
+      cp_fwd_kernel<3, T, VWV, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part);
+    else if (N == 4)
+      cp_fwd_kernel<4, T, VWV, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part);
+    else
+      cp_fwd_kernel<0, T, VWV, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part);
+  } else {
+    switch (c.RC) {
+      case 1: cp_fwd_kernel<0, T, 1, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part); break;
+      case 2: cp_fwd_kernel<0, T, 1, 2><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part); break;
+      case 4: cp_fwd_kernel<0, T, 1, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part); break;
+      default: cp_fwd_kernel<0, T, 1, 8><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part); break;
+    }
+  }
+  return SPM_OK;
+}
+
+int launch_cp_fwd(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N,
+                  const FactorPtrs& fp, int R, int dtype, double* part, int nb, float* loss,
+                  double* loss64, cudaStream_t s) {
+  bool aligned = true;
+  for (int k = 0; k < N; ++k) aligned = aligned && (((uintptr_t)fp.p[k] & 15u) == 0);
+  if (dtype == SPM_DTYPE_BF16)
+    fwd_dispatch<__nv_bfloat16>(elems, res, nnz, es, N, fp, R, aligned, part, nb, s);
+  else
+    fwd_dispatch<float>(elems, res, nnz, es, N, fp, R, aligned, part, nb, s);
+  cp_loss_final_kernel<<<1, 32, 0, s>>>(part, nb, loss, loss64);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "cp_fwd kernels");
+}
+
+}  // namespace spm

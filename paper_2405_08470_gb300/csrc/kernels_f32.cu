@@ -1,9 +1,29 @@
 // kernels_f32.cu - FP32-factor instantiations of the fused spMTTKRP + remap kernel.
+#include "mttkrp_direct.cuh"
 #include "mttkrp_kernel.cuh"
 
 namespace spm {
 
+static int launch_direct_float(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
+  if (c.vec) {
+    switch (a.nmodes) {
+      case 3: return launch_direct<3, float, 4, 1, 4>(a, c.L, s);
+      case 4: return launch_direct<4, float, 4, 1, 4>(a, c.L, s);
+      case 5: return launch_direct<5, float, 4, 1, 4>(a, c.L, s);
+      case 6: return launch_direct<6, float, 4, 1, 4>(a, c.L, s);
+      default: return launch_direct<0, float, 4, 1, 2>(a, c.L, s);
+    }
+  }
+  switch (c.RC) {
+    case 1: return launch_direct<0, float, 1, 1, 2>(a, c.L, s);
+    case 2: return launch_direct<0, float, 1, 2, 2>(a, c.L, s);
+    case 4: return launch_direct<0, float, 1, 4, 2>(a, c.L, s);
+    default: return launch_direct<0, float, 1, 8, 2>(a, c.L, s);
+  }
+}
+
 int launch_mttkrp_f32(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
+  if (a.variant == 0) return launch_direct_float(a, c, s);
   if (c.vec) {
     switch (a.nmodes) {
       case 3: return launch_variant<3, float, 4, 1>(a, c.L, s);

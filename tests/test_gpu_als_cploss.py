@@ -1,0 +1,155 @@
+"""GPU parity of CP-ALS, the CP loss / gradient and the autotuner against the oracle."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+from paper_2405_08470_gb300 import Plan, SpmError
+from paper_2405_08470_gb300.cp import CPLoss, cp_als
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("dims,R,nnz", [((200, 150, 100), 16, 50_000),
+                                        ((40, 30, 20, 10), 8, 6_000),
+                                        ((30, 20, 12, 8, 6), 8, 4_000)])
+def test_als_iterations_match_oracle(dims, R, nnz):
+    N = len(dims)
+    coo, vals = synth.make_coo(dims, nnz, (0.0,) * N, seed=nnz + N)
+    c, v = coo.numpy(), vals.numpy()
+    F0 = synth.make_factors(dims, R, seed=2000)
+    Fd = [f.cuda() for f in F0]
+    Fo = [f.numpy().astype(np.float64) for f in F0]
+    p = Plan(c, v, dims, R, nblk=37)
+    lam = torch.empty(R, device="cuda")
+    for it in range(5):
+        fit = p.als_iter(Fd, lam)           # first call eager, later calls graph replays
+        Fo, lo, fo = O.cp_als_iter(c, v, dims, Fo)
+        assert abs(fit - fo) <= 1e-5, (it, fit, fo)
+        assert O.relerr(lam.cpu().numpy(), lo) <= 1e-4
+        for k in range(N):
+            assert O.relerr(Fd[k].cpu().numpy(), Fo[k]) <= 1e-4, (it, k)
+    p.close()
+
+
+def test_als_fit_never_decreases_and_bf16_runs():
+    dims, R = (120, 90, 60), 8
+    coo, vals = synth.make_coo(dims, 20_000, (1.1, 1.1, 0.0), seed=3)
+    p = Plan(coo.numpy(), vals.numpy(), dims, R)
+    F = [f.cuda() for f in synth.make_factors(dims, R, seed=4)]
+    _, fits = cp_als(p, F, 8)
+    assert all(b >= a - 1e-6 for a, b in zip(fits, fits[1:])), fits
+    p.close()
+    pb = Plan(coo.numpy(), vals.numpy(), dims, R, dtype="bf16")
+    Fb = [f.cuda().to(torch.bfloat16) for f in synth.make_factors(dims, R, seed=4)]
+    _, fb = cp_als(pb, Fb, 8)
+    assert abs(fb[-1] - fits[-1]) < 2e-2
+    pb.close()
+
+
+def test_als_not_spd_is_a_status_not_a_fault():
+    dims, R = (20, 15, 10), 4
+    coo, vals = synth.make_coo(dims, 500, (0.0,) * 3, seed=8)
+    p = Plan(coo.numpy(), vals.numpy(), dims, R)
+    F = [f.cuda() for f in synth.make_factors(dims, R, seed=9)]
+    F[1][:, 2] = 0.0           # zero column: V for mode 0 is singular
+    lam = torch.empty(R, device="cuda")
+    with pytest.raises(SpmError) as ei:
+        p.als_iter(F, lam)
+    assert ei.value.status == -7
+    # the plan stays usable
+    G = [f.cuda() for f in synth.make_factors(dims, R, seed=9)]
+    fit = p.als_iter(G, lam)
+    assert np.isfinite(fit)
+    p.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_cp_loss_and_gradient_match_oracle(dtype):
+    dims, R = (80, 60, 40), 16
+    coo, _ = synth.make_coo(dims, 12_000, (1.1, 1.1, 1.1), seed=21)
+    x = synth.make_planted_targets(coo, dims, 8, 0.1, seed=22)
+    c, xv = coo.numpy(), x.numpy()
+    F = synth.make_factors(dims, R, seed=23, scale=0.3)
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+    Fd = [f.to(tdt).cuda().requires_grad_(True) for f in F]
+    Fq = [f.to(tdt).float().numpy().astype(np.float64) for f in F]
+    p = Plan(c, xv, dims, R, dtype=dtype, nblk=19)
+    loss = CPLoss.apply(p, *Fd)
+    loss.backward()
+    want_loss, _ = O.cp_loss(c, xv, Fq)
+    assert abs(loss.item() - want_loss) <= 1e-5 * abs(want_loss)
+    G = O.cp_loss_grad(c, xv, dims, Fq)
+    for k in range(3):
+        got = Fd[k].grad.float().cpu().numpy()
+        tol = 1e-5 if dtype == "f32" else 1e-2
+        assert O.relerr(got, G[k]) <= tol, (k, O.relerr(got, G[k]))
+    if dtype == "bf16":  # quantisation error against the FP32 factors
+        G32 = O.cp_loss_grad(c, xv, dims, [f.numpy().astype(np.float64) for f in F])
+        for k in range(3):
+            assert O.relerr(Fd[k].grad.float().cpu().numpy(), G32[k]) <= 5e-2
+    p.close()
+
+
+def test_cp_loss_gradient_finite_differences_small_copy():
+    spec = synth.workload("c5fd")
+    coo, _ = synth.make_coo(spec.dims, spec.nnz, spec.skew, spec.seed)
+    x = synth.make_planted_targets(coo, spec.dims, 8, 0.1, spec.seed + 1)
+    F = synth.make_factors(spec.dims, 8, seed=3000, scale=0.5)
+    p = Plan(coo.numpy(), x.numpy(), spec.dims, 8)
+    Fd = [f.cuda().requires_grad_(True) for f in F]
+    loss = CPLoss.apply(p, *Fd)
+    loss.backward()
+    Fo = [f.numpy().astype(np.float64) for f in F]
+    rng = np.random.default_rng(5)
+    h = 1e-3
+    for k in range(3):
+        for _ in range(5):
+            i, r = int(rng.integers(spec.dims[k])), int(rng.integers(8))
+            Fp = [f.copy() for f in Fo]
+            Fm = [f.copy() for f in Fo]
+            Fp[k][i, r] += h
+            Fm[k][i, r] -= h
+            fd = (O.cp_loss(coo.numpy(), x.numpy(), Fp)[0] -
+                  O.cp_loss(coo.numpy(), x.numpy(), Fm)[0]) / (2 * h)
+            got = Fd[k].grad[i, r].item()
+            assert abs(got - fd) <= 1e-4 * max(1.0, abs(fd)), (k, i, r, got, fd)
+    p.close()
+
+
+def test_autotune_keeps_results_and_caches(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SPMTTKRP_TUNE_CACHE", str(cache))
+    dims, R = (3000, 2000, 1000), 32
+    coo, vals = synth.make_coo(dims, 300_000, (1.1, 1.1, 1.1), seed=31, device="cuda")
+    c, v = coo.cpu().numpy(), vals.cpu().numpy()
+    F = [f.cuda() for f in synth.make_factors(dims, R, seed=32)]
+    p = Plan(c, v, dims, R)
+    scratch = [torch.empty(d, R, device="cuda") for d in dims]
+    p.autotune(F, scratch)
+    assert cache.exists() and cache.read_text().strip()
+    outs = [torch.full((d, R), float("nan"), device="cuda") for d in dims]
+    p.sweep(F, outs)
+    torch.cuda.synchronize()
+    Fh = [f.cpu().numpy() for f in F]
+    for n in range(3):
+        rows = np.unique(np.concatenate([c[:50, n], [0, dims[n] - 1]]))
+        want = O.mttkrp_rows(c, v, Fh, n, rows)
+        assert O.relerr(outs[n].cpu().numpy()[rows], want) <= 1e-5
+    # a second plan of the same shape picks the cached configuration
+    p2 = Plan(c, v, dims, R)
+    p2.autotune(F, scratch)
+    assert p2.info()["nblk"] == p.info()["nblk"]
+    p.close()
+    p2.close()
