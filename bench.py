@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--nnz", type=int, default=0, help="override nonzero count (small runs)")
     ap.add_argument("--nblk", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--variant", type=int, default=0, help="0 direct runs, 1 staged tiles")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="0 warp blocks with staged tiles, 1 CTA blocks with direct runs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -367,7 +368,8 @@ def main():
             "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": spec.name, "dims": list(spec.dims), "nnz": nnz, "rank": R,
                        "factor_dtype": args.dtype, "nblk": info["nblk"], "tile": info["tile"],
-                       "kernel_form": ["direct runs", "staged tiles"][args.variant],
+                       "kernel_form": ["warp blocks, bulk-async staged tiles",
+                                       "CTA blocks, direct runs"][args.variant],
                        "l2": "inputs larger than L2 (element stream "
                              f"{nnz * info['elem_bytes'] / 1e9:.2f} GB per mode)",
                        "parallelism": f"replicas x{world}"},

@@ -57,17 +57,18 @@ enum spm_dtype { SPM_DTYPE_F32 = 0, SPM_DTYPE_BF16 = 1 };
 typedef struct {
   int factor_dtype; /* SPM_DTYPE_F32 or SPM_DTYPE_BF16 (factor storage only)     */
   int partition;    /* 0 = contiguous split with heavy-row splitting (only one)  */
-  int nblk;         /* blocks per mode; 0 = size-based default                    */
-  int tile;         /* nonzeros staged per shared-memory tile: 0 (=512), 256, 512,
-                       1024                                                        */
+  int nblk;         /* blocks per mode (warp blocks for variant 0, CTA blocks for
+                       variant 1); 0 = size-based default                         */
+  int tile;         /* nonzeros per staged warp tile: 0 (= 128 for 3 modes, less
+                       for wider elements), 32, 64, 128 or 256                    */
   size_t max_bytes; /* cap on the plan's device memory; 0 = no cap               */
   int checks;       /* 1 = synchronize and read the device error word after every
                        compute call (slow; for debugging)                         */
   int host_only;    /* 1 = build the plan on the host only (no device memory);
                        only spmttkrp_plan_query and destroy are then valid        */
-  int variant;      /* fused kernel form: 0 = each lane group streams one long
-                       contiguous run (default), 1 = tiles staged in shared memory
-                       by bulk async copies                                       */
+  int variant;      /* fused kernel form: 0 = one warp per block, tiles staged in
+                       shared memory by bulk async copies (default); 1 = one CTA
+                       per block, each lane group streams one contiguous run     */
   void* stream;     /* cudaStream_t for all work; NULL = default stream           */
 } spmttkrp_opts_t;
 

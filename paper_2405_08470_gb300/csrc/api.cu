@@ -212,8 +212,8 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     return fail(SPM_ERR_INVALID_ARG, "factor_dtype must be F32 or BF16");
   if (o.partition != 0)
     return fail(SPM_ERR_UNSUPPORTED, "only the contiguous split (partition 0) is built");
-  if (o.tile != 0 && o.tile != 256 && o.tile != 512 && o.tile != 1024)
-    return fail(SPM_ERR_INVALID_ARG, "tile must be 0, 256, 512 or 1024");
+  if (o.tile != 0 && o.tile != 32 && o.tile != 64 && o.tile != 128 && o.tile != 256)
+    return fail(SPM_ERR_INVALID_ARG, "tile must be 0, 32, 64, 128 or 256");
   if (o.nblk < 0) return fail(SPM_ERR_INVALID_ARG, "nblk must be >= 0");
   if (o.variant != 0 && o.variant != 1) return fail(SPM_ERR_INVALID_ARG, "variant must be 0 or 1");
 
@@ -223,7 +223,6 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->R = rank;
   p->nnz = nnz;
   p->dtype = o.factor_dtype;
-  p->tile = o.tile ? o.tile : 512;
   p->variant = o.variant;
   p->checks = o.checks;
   p->host_only = o.host_only;
@@ -231,8 +230,9 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->stream = (cudaStream_t)o.stream;
   p->dims.assign(dims, dims + nmodes);
   p->es = ((4 * nmodes + 4) + 15) & ~15;
+  p->tile = o.tile ? o.tile : default_tile(p->es);
   // keep the staged tiles within shared memory for wide elements
-  while (p->tile > 256 && mttkrp_smem_bytes(p->es, p->tile, p->R, p->dtype) > 200 * 1024)
+  while (p->tile > 32 && mttkrp_smem_bytes(p->es, p->tile, p->R, p->dtype) > 200 * 1024)
     p->tile /= 2;
   if (!p->host_only) {
     cudaError_t e = cudaGetDevice(&p->device);

@@ -279,17 +279,18 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   struct Cand {
     int nps, tile, variant;
   };
+  // blocks per SM: warp blocks (form 0) in multiples of 24 resident warps,
+  // CTA blocks (form 1) in multiples of 4
   std::vector<Cand> cands;
-  for (int v : {0, 1})
-    for (int n : {2, 4, 8, 16, 32, 64}) {
-      if (n > 4 && (int64_t)n * p->num_sms * 256 > p->nnz) continue;
-      if (v == 0) {
-        cands.push_back({n, p->tile, 0});
-      } else {
-        for (int t : {256, 512, 1024})
-          if (mttkrp_smem_bytes(p->es, t, p->R, p->dtype) <= 200 * 1024) cands.push_back({n, t, 1});
-      }
-    }
+  for (int n : {24, 48, 96, 192}) {
+    if ((int64_t)n * p->num_sms * 128 > p->nnz && n > 24) continue;
+    for (int t : {64, 128, 256})
+      if (mttkrp_smem_bytes(p->es, t, p->R, p->dtype) <= 200 * 1024) cands.push_back({n, t, 0});
+  }
+  for (int n : {4, 8, 16, 32}) {
+    if ((int64_t)n * p->num_sms * 1024 > p->nnz && n > 4) continue;
+    cands.push_back({n, p->tile, 1});
+  }
   cudaEvent_t e0, e1;
   SPM_CUDA(cudaEventCreate(&e0));
   SPM_CUDA(cudaEventCreate(&e1));

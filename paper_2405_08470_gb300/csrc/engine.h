@@ -59,7 +59,7 @@ struct GraphCache {
 
 struct spmttkrp_plan {
   int N = 0, R = 0, dtype = 0, tile = 512, checks = 0, host_only = 0;
-  int variant = 0;  // fused-kernel form: 0 = direct runs, 1 = staged tiles
+  int variant = 0;  // fused-kernel form: 0 = warp blocks, staged tiles; 1 = CTA blocks, direct runs
   int64_t nnz = 0;
   int es = 16;  // element stride in bytes: {int32 idx[N]; float val}, rounded up to 16
   std::vector<int64_t> dims;
@@ -115,8 +115,9 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // ---- host planning (plan_host.cpp) ----
 int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int nblk_opt);
+int default_tile(int es);
 int partition_mode(const spmttkrp_plan* p, int n, int nblk, ModeHost* out);
-int default_nblk(int64_t nnz, int num_sms);
+int default_nblk(int64_t nnz, int num_sms, int variant);
 
 // ---- kernel launchers (kernels_*.cu) ----
 struct MttkrpArgs {
@@ -134,7 +135,7 @@ struct MttkrpArgs {
   int* err;
   const float* scale;      // device scalar multiplier or null
   int dtype;
-  int variant;             // 0 = direct runs, 1 = staged tiles
+  int variant;             // 0 = warp blocks, staged tiles; 1 = CTA blocks, direct runs
 };
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
 int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* out,

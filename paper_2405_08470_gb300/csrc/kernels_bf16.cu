@@ -24,21 +24,21 @@ static int launch_direct_bfloat16(const MttkrpArgs& a, const LaneCfg& c, cudaStr
 }
 
 int launch_mttkrp_bf16(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
-  if (a.variant == 0) return launch_direct_bfloat16(a, c, s);
+  if (a.variant == 1) return launch_direct_bfloat16(a, c, s);
   if (c.vec) {
     switch (a.nmodes) {
-      case 3: return launch_variant<3, __nv_bfloat16, 8, 1>(a, c.L, s);
-      case 4: return launch_variant<4, __nv_bfloat16, 8, 1>(a, c.L, s);
-      case 5: return launch_variant<5, __nv_bfloat16, 8, 1>(a, c.L, s);
-      case 6: return launch_variant<6, __nv_bfloat16, 8, 1>(a, c.L, s);
-      default: return launch_variant<0, __nv_bfloat16, 8, 1>(a, c.L, s);
+      case 3: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
+      case 4: return launch_warp_kernel<4, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
+      case 5: return launch_warp_kernel<5, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
+      case 6: return launch_warp_kernel<6, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
+      default: return launch_warp_kernel<0, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
     }
   }
   switch (c.RC) {
-    case 1: return launch_variant<0, __nv_bfloat16, 1, 1>(a, c.L, s);
-    case 2: return launch_variant<0, __nv_bfloat16, 1, 2>(a, c.L, s);
-    case 4: return launch_variant<0, __nv_bfloat16, 1, 4>(a, c.L, s);
-    default: return launch_variant<0, __nv_bfloat16, 1, 8>(a, c.L, s);
+    case 1: return launch_warp_kernel<0, __nv_bfloat16, 1, 1, 4>(a, c.L, s);
+    case 2: return launch_warp_kernel<0, __nv_bfloat16, 1, 2, 4>(a, c.L, s);
+    case 4: return launch_warp_kernel<0, __nv_bfloat16, 1, 4, 2>(a, c.L, s);
+    default: return launch_warp_kernel<0, __nv_bfloat16, 1, 8, 1>(a, c.L, s);
   }
 }
 

@@ -23,21 +23,21 @@ static int launch_direct_float(const MttkrpArgs& a, const LaneCfg& c, cudaStream
 }
 
 int launch_mttkrp_f32(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
-  if (a.variant == 0) return launch_direct_float(a, c, s);
+  if (a.variant == 1) return launch_direct_float(a, c, s);
   if (c.vec) {
     switch (a.nmodes) {
-      case 3: return launch_variant<3, float, 4, 1>(a, c.L, s);
-      case 4: return launch_variant<4, float, 4, 1>(a, c.L, s);
-      case 5: return launch_variant<5, float, 4, 1>(a, c.L, s);
-      case 6: return launch_variant<6, float, 4, 1>(a, c.L, s);
-      default: return launch_variant<0, float, 4, 1>(a, c.L, s);
+      case 3: return launch_warp_kernel<3, float, 4, 1, 8>(a, c.L, s);
+      case 4: return launch_warp_kernel<4, float, 4, 1, 8>(a, c.L, s);
+      case 5: return launch_warp_kernel<5, float, 4, 1, 8>(a, c.L, s);
+      case 6: return launch_warp_kernel<6, float, 4, 1, 8>(a, c.L, s);
+      default: return launch_warp_kernel<0, float, 4, 1, 8>(a, c.L, s);
     }
   }
   switch (c.RC) {
-    case 1: return launch_variant<0, float, 1, 1>(a, c.L, s);
-    case 2: return launch_variant<0, float, 1, 2>(a, c.L, s);
-    case 4: return launch_variant<0, float, 1, 4>(a, c.L, s);
-    default: return launch_variant<0, float, 1, 8>(a, c.L, s);
+    case 1: return launch_warp_kernel<0, float, 1, 1, 4>(a, c.L, s);
+    case 2: return launch_warp_kernel<0, float, 1, 2, 4>(a, c.L, s);
+    case 4: return launch_warp_kernel<0, float, 1, 4, 2>(a, c.L, s);
+    default: return launch_warp_kernel<0, float, 1, 8, 1>(a, c.L, s);
   }
 }
 

@@ -17,11 +17,12 @@ static LaneCfg cfg_for(const MttkrpArgs& a) {
 }
 
 size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype) {
-  LaneCfg c = lane_config(R, dtype, true);
-  LaneCfg c2 = lane_config(R, dtype, false);
-  int NG = (kThreads / 32) * (32 / c.L);
-  int NG2 = (kThreads / 32) * (32 / c2.L);
-  return std::max(smem_layout(es, tile, R, NG).total, smem_layout(es, tile, R, NG2).total);
+  size_t m = 0;
+  for (bool al : {true, false}) {
+    const LaneCfg c = lane_config(R, dtype, al);
+    m = std::max(m, (size_t)kWarps * warp_layout(es, tile, R, 32 / c.L).total);
+  }
+  return m;
 }
 
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s) {

@@ -1,0 +1,156 @@
+// mttkrp_common.cuh - helpers shared by the fused spMTTKRP + remap kernels:
+// lane layout of a rank-R row over a group of lanes, bulk-async copy and
+// mbarrier PTX wrappers with bounded waits, and 16-byte factor-row loads.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "engine.h"
+
+namespace spm {
+
+
+struct LaneCfg {
+  int L;    // lanes per nonzero (power of two <= 32)
+  int VW;   // elements per lane per load (4 fp32 / 8 bf16 for 16-byte loads, else 1)
+  int RC;   // rank chunks per lane for the scalar path
+  bool vec;
+};
+
+__host__ __device__ inline int pow2ceil(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+inline LaneCfg lane_config(int R, int dtype, bool aligned16) {
+  LaneCfg c;
+  int vw = dtype == SPM_DTYPE_BF16 ? 8 : 4;
+  if (aligned16 && R % vw == 0 && R / vw <= 32) {
+    c.vec = true;
+    c.VW = vw;
+    c.L = pow2ceil(R / vw);
+    c.RC = 1;
+  } else {
+    c.vec = false;
+    c.VW = 1;
+    if (R <= 32) {
+      c.L = pow2ceil(R);
+      c.RC = 1;
+    } else {
+      c.L = 32;
+      c.RC = pow2ceil((R + 31) / 32);
+    }
+  }
+  return c;
+}
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1D bulk async copy global -> shared, completes `bytes` on the mbarrier.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2 s and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  const uint64_t t0 = global_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > 2000000000ull) return false;
+  }
+}
+
+// ------------------------------------------------------------ factor slices
+
+template <typename T, int VW>
+struct Slice;
+
+template <>
+struct Slice<float, 4> {
+  __device__ __forceinline__ static void load(const void* base, int64_t row, int R, int sub,
+                                              float* x) {
+    const float4 v =
+        __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(base) + row * R) + sub);
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+  }
+};
+
+template <>
+struct Slice<__nv_bfloat16, 8> {
+  __device__ __forceinline__ static void load(const void* base, int64_t row, int R, int sub,
+                                              float* x) {
+    const uint4 v = __ldg(
+        reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * R) + sub);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      x[2 * j] = __uint_as_float(w[j] << 16);
+      x[2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+    }
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ float load_scalar(const void* base, int64_t idx);
+template <>
+__device__ __forceinline__ float load_scalar<float>(const void* base, int64_t idx) {
+  return __ldg(static_cast<const float*>(base) + idx);
+}
+template <>
+__device__ __forceinline__ float load_scalar<__nv_bfloat16>(const void* base, int64_t idx) {
+  const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(base) + idx);
+  return __uint_as_float((uint32_t)u << 16);
+}
+
+}  // namespace spm

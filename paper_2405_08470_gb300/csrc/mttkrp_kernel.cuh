@@ -1,247 +1,105 @@
-// mttkrp_kernel.cuh - the fused mode-n spMTTKRP + dynamic remap kernel.
+// mttkrp_kernel.cuh - the fused mode-n spMTTKRP + dynamic remap kernel,
+// one warp per block of the split.
 //
-// One CTA owns one block [lo, hi) of the mode-n ordered working copy (the
-// paper's thread block over a tensor partition, Algorithm 4).  Its nonzeros
-// are streamed through shared memory in tiles by 1D bulk-async copies
-// (cp.async.bulk, completion on an mbarrier, three buffers, two tiles in
-// flight).  For every tile:
-//   * remap (Algorithm 3): every thread copies elements to their place in
-//     the next mode's order, T_out[next_pos[p]] = x_p;
-//   * elementwise computation (Algorithm 2): the CTA is cut into groups of L
+// Every warp owns one block [lo, hi) of the mode-n ordered working copy (the
+// paper's thread block over a tensor partition, Algorithm 4, shrunk to a warp
+// so that no CTA-wide synchronisation is ever needed).  The warp streams its
+// block through its own shared-memory ring: lane 0 issues 1D bulk-async
+// copies (cp.async.bulk) of the nonzeros and of their remap ids two tiles
+// ahead, completion is signalled on per-warp mbarriers, and every wait is
+// bounded.  For every tile:
+//   * remap (Algorithm 3): the 32 lanes copy the tile's nonzeros to their
+//     places in the next mode's order, T_out[next_pos[p]] = x_p;
+//   * elementwise computation (Algorithm 2): the warp is cut into groups of L
 //     lanes, each lane owning a 16-byte slice of a rank-R row; a group walks
-//     a contiguous run of the tile, gathers A_k[i_k, slice] for k != n with
-//     16-byte read-only loads, forms val * Hadamard product, and accumulates
-//     it in registers while the output row stays the same;
-//   * rows that start and end inside one run are written straight to M_n;
-//     a run's first and last rows leave partial sums in shared-memory slots
-//     that one warp adds in run order on the next tile (carrying the row
-//     that continues into the following tile).
-// A row that continues past the block's end is written as a partial to
-// `part` and summed by the fix-up kernel in block order.  Nothing is added
-// atomically, so results are bit-identical from run to run, and every output
-// row is written exactly once (rows without nonzeros are zero-filled by the
-// writer of the next nonempty row, or of the last one).
+//     a contiguous run of the tile U nonzeros at a time, issues the factor-row
+//     gathers A_k[i_k, slice] (k != n, 16-byte read-only loads; the indices
+//     come from shared memory, so all U x (N-1) gathers leave at once), and
+//     accumulates val * Hadamard product in registers while the output row
+//     is unchanged; rows that start and end inside the run are written
+//     straight to M_n;
+//   * the first and last row of every run leave partial sums in shared-memory
+//     slots, which the warp adds in run order, carrying the row that
+//     continues into the next tile in registers.
+// A row that continues past the block is written as a partial to `part` and
+// summed by the fix-up kernel in block order.  No atomics: results are
+// bit-identical from run to run and every output row is written exactly once
+// (empty rows are zero-filled by the writer of the next nonempty row, or of
+// the last one).
 #pragma once
 
-#include <cuda_bf16.h>
-#include <stdint.h>
-
-#include <algorithm>
-
-#include "engine.h"
+#include "mttkrp_common.cuh"
 
 namespace spm {
 
-constexpr int kNBuf = 3;  // element tile buffers (two tiles in flight)
+constexpr int kStages = 3;  // tiles per warp ring (two in flight while one is used)
+constexpr int kWarps = kThreads / 32;
 
-struct LaneCfg {
-  int L;    // lanes per nonzero (power of two <= 32)
-  int VW;   // elements per lane per load (4 fp32 / 8 bf16 for 16-byte loads, else 1)
-  int RC;   // rank chunks per lane for the scalar path
-  bool vec;
+// Per-warp shared-memory layout (bytes, in order).
+struct WarpLayout {
+  size_t ebuf, npbuf, sacc, cacc, srow, sprev, mbar, total;
 };
 
-__host__ __device__ inline int pow2ceil(int x) {
-  int p = 1;
-  while (p < x) p <<= 1;
-  return p;
-}
-
-inline LaneCfg lane_config(int R, int dtype, bool aligned16) {
-  LaneCfg c;
-  int vw = dtype == SPM_DTYPE_BF16 ? 8 : 4;
-  if (aligned16 && R % vw == 0 && R / vw <= 32) {
-    c.vec = true;
-    c.VW = vw;
-    c.L = pow2ceil(R / vw);
-    c.RC = 1;
-  } else {
-    c.vec = false;
-    c.VW = 1;
-    if (R <= 32) {
-      c.L = pow2ceil(R);
-      c.RC = 1;
-    } else {
-      c.L = 32;
-      c.RC = pow2ceil((R + 31) / 32);
-    }
-  }
-  return c;
-}
-
-// Shared-memory layout of the fused kernel (bytes, in order).
-struct SmemLayout {
-  size_t ebuf, npbuf, sacc, srow, sprev, cacc, cmeta, mbar, total;
-};
-
-__host__ __device__ inline SmemLayout smem_layout(int es, int tile, int R, int NG) {
-  SmemLayout l;
+__host__ __device__ inline WarpLayout warp_layout(int es, int tw, int R, int G) {
+  WarpLayout l;
   size_t o = 0;
   l.ebuf = o;
-  o += (size_t)kNBuf * tile * es;
+  o += (size_t)kStages * tw * es;
   l.npbuf = o;
-  o += (size_t)kNBuf * (tile + 8) * 4;
+  o += (size_t)kStages * (tw + 8) * 4;
   l.sacc = o;
-  o += (size_t)2 * 2 * NG * R * 4;
-  l.srow = o;
-  o += (size_t)2 * 2 * NG * 4;
-  l.sprev = o;
-  o += (size_t)2 * 2 * NG * 4;
+  o += (size_t)2 * G * R * 4;
   l.cacc = o;
   o += (size_t)R * 4;
-  l.cmeta = o;
-  o += 16;
+  l.srow = o;
+  o += (size_t)2 * G * 4;
+  l.sprev = o;
+  o += (size_t)2 * G * 4;
   o = (o + 7) & ~(size_t)7;
   l.mbar = o;
-  o += (size_t)kNBuf * 8;
+  o += (size_t)kStages * 8;
   l.total = (o + 127) & ~(size_t)127;
   return l;
 }
 
-// ------------------------------------------------------------ PTX helpers
+// Default nonzeros per warp tile: small enough that three CTAs of 8 warps fit an SM.
+__host__ __device__ inline int warp_tile(int es) { return es <= 16 ? 128 : (es <= 32 ? 64 : 32); }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// 1D bulk async copy global -> shared, completes `bytes` on the mbarrier.
-// Both addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait on an mbarrier phase: gives up after ~2 s and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  const uint64_t t0 = global_ns();
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (global_ns() - t0 > 2000000000ull) return false;
-  }
-}
-
-// ------------------------------------------------------------ factor slices
-
-template <typename T, int VW>
-struct Slice;
-
-template <>
-struct Slice<float, 4> {
-  __device__ __forceinline__ static void load(const void* base, int64_t row, int R, int sub,
-                                              float* x) {
-    const float4 v =
-        __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(base) + row * R) + sub);
-    x[0] = v.x;
-    x[1] = v.y;
-    x[2] = v.z;
-    x[3] = v.w;
-  }
-};
-
-template <>
-struct Slice<__nv_bfloat16, 8> {
-  __device__ __forceinline__ static void load(const void* base, int64_t row, int R, int sub,
-                                              float* x) {
-    const uint4 v = __ldg(
-        reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * R) + sub);
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      x[2 * j] = __uint_as_float(w[j] << 16);
-      x[2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
-    }
-  }
-};
-
-template <typename T>
-__device__ __forceinline__ float load_scalar(const void* base, int64_t idx);
-template <>
-__device__ __forceinline__ float load_scalar<float>(const void* base, int64_t idx) {
-  return __ldg(static_cast<const float*>(base) + idx);
-}
-template <>
-__device__ __forceinline__ float load_scalar<__nv_bfloat16>(const void* base, int64_t idx) {
-  const unsigned short u = __ldg(reinterpret_cast<const unsigned short*>(base) + idx);
-  return __uint_as_float((uint32_t)u << 16);
-}
-
-// ------------------------------------------------------------ the kernel
-
-// NT: number of modes at compile time (0 = runtime).  T: factor type.
-// VW: values per lane per load (vector path) or 1 (scalar path).
-// RC: rank chunks per lane (scalar path; 1 on the vector path).
-template <int NT, typename T, int VW, int RC>
-__global__ void __launch_bounds__(kThreads) mttkrp_remap_kernel(const MttkrpArgs a, const int L) {
-  constexpr int NV = VW * RC;  // accumulator values per lane
-  constexpr int U = (VW > 1) ? 4 : 2;  // nonzeros in flight per group
+template <int NT, typename T, int VW, int RC, int U>
+__global__ void __launch_bounds__(kThreads) mttkrp_warp_kernel(const MttkrpArgs a, const int L) {
+  constexpr int NV = VW * RC;
   const int N = NT > 0 ? NT : a.nmodes;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int G = 32 / L, NG = (kThreads / 32) * G;
-  const int tile = a.tile, K = tile / NG, es = a.es, R = a.R, mode = a.mode;
-  const int sub = lane % L, gw = lane / L, gi = warp * G + gw;
-
-  extern __shared__ __align__(128) uint8_t smem[];
-  const SmemLayout lay = smem_layout(es, tile, R, NG);
-  uint8_t* ebuf = smem + lay.ebuf;
-  int32_t* npbuf = reinterpret_cast<int32_t*>(smem + lay.npbuf);
-  float* sacc = reinterpret_cast<float*>(smem + lay.sacc);
-  int* srow = reinterpret_cast<int*>(smem + lay.srow);
-  int* sprev = reinterpret_cast<int*>(smem + lay.sprev);
-  float* cacc = reinterpret_cast<float*>(smem + lay.cacc);
-  int* cmeta = reinterpret_cast<int*>(smem + lay.cmeta);  // carry row, carry prev, emitted, status
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + lay.mbar);
-
-  const int4 bi = a.blkinfo[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = 32 / L, sub = lane % L, gw = lane / L;
+  const int es = a.es, R = a.R, mode = a.mode;
+  const int TW = a.tile, K = TW / G;
+  const int wb = blockIdx.x * kWarps + warp;
+  if (wb >= a.nblk) return;
+  const int4 bi = a.blkinfo[wb];
   const int lo = bi.x, hi = bi.y;
   if (lo >= hi) return;
-  const int ntiles = (hi - lo + tile - 1) / tile;
+
+  extern __shared__ __align__(128) uint8_t smem[];
+  const WarpLayout lay = warp_layout(es, TW, R, G);
+  uint8_t* wbase = smem + (size_t)warp * lay.total;
+  uint8_t* ebuf = wbase + lay.ebuf;
+  int32_t* npbuf = reinterpret_cast<int32_t*>(wbase + lay.npbuf);
+  float* sacc = reinterpret_cast<float*>(wbase + lay.sacc);
+  float* cacc = reinterpret_cast<float*>(wbase + lay.cacc);  // carry row partial (lanes over R)
+  int* srow = reinterpret_cast<int*>(wbase + lay.srow);
+  int* sprev = reinterpret_cast<int*>(wbase + lay.sprev);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(wbase + lay.mbar);
+
+  const int ntiles = (hi - lo + TW - 1) / TW;
   const bool remap = a.elems_out != nullptr;
   const float sc = a.scale ? __ldg(a.scale) : 1.0f;
   const int64_t out_rows = a.out_rows;
   float* __restrict__ out = a.out;
 
-  auto issue = [&](int t) {
-    const int buf = t % kNBuf;
-    const int tlo = lo + t * tile;
-    const int n = min(tile, hi - tlo);
+  auto issue = [&](int t) {  // lane 0 only
+    const int st = t % kStages;
+    const int tlo = lo + t * TW;
+    const int n = min(TW, hi - tlo);
     const uint32_t ebytes = (uint32_t)n * es;
     uint32_t npbytes = 0;
     int np0 = 0;
@@ -250,32 +108,26 @@ __global__ void __launch_bounds__(kThreads) mttkrp_remap_kernel(const MttkrpArgs
       npbytes = ((uint32_t)(tlo + n - np0) * 4u + 15u) & ~15u;
     }
     fence_proxy_async_smem();
-    mbar_expect_tx(&mbar[buf], ebytes + npbytes);
-    bulk_g2s(ebuf + (size_t)buf * tile * es, a.elems_in + (size_t)tlo * es, ebytes, &mbar[buf]);
-    if (remap) bulk_g2s(npbuf + buf * (tile + 8), a.next_pos + np0, npbytes, &mbar[buf]);
+    mbar_expect_tx(&mbar[st], ebytes + npbytes);
+    bulk_g2s(ebuf + (size_t)st * TW * es, a.elems_in + (size_t)tlo * es, ebytes, &mbar[st]);
+    if (remap) bulk_g2s(npbuf + st * (TW + 8), a.next_pos + np0, npbytes, &mbar[st]);
   };
 
-  if (tid == 0) {
-    for (int b = 0; b < kNBuf; ++b) mbar_init(&mbar[b], 1);
+  if (lane == 0) {
+    for (int b = 0; b < kStages; ++b) mbar_init(&mbar[b], 1);
     fence_mbar_init();
-    cmeta[0] = -1;    // carry row: none yet
-    cmeta[1] = bi.z;  // row before the carry row (row before the block)
-    cmeta[2] = 0;     // no row emitted yet
-    cmeta[3] = 0;     // status
   }
-  for (int r = tid; r < R; r += kThreads) cacc[r] = 0.f;
-  __syncthreads();
-  if (tid == 0) {
+  __syncwarp();
+  if (lane == 0) {
     issue(0);
     if (ntiles > 1) issue(1);
   }
 
-  // ---- helpers: rank slices owned by a lane of a group
-  auto rank_of = [&](int j) -> int {  // j in [0, NV): rank index of accumulator slot j
+  auto rank_of = [&](int j) -> int {
     if constexpr (VW > 1) return sub * VW + j;
     return sub + L * j;
   };
-  auto zero_rows_group = [&](int64_t from, int64_t to) {  // rows [from, to)
+  auto zero_rows_group = [&](int64_t from, int64_t to) {
     for (int64_t z = from; z < to; ++z) {
       if constexpr (VW > 1) {
         if (sub * VW < R) {
@@ -311,122 +163,64 @@ __global__ void __launch_bounds__(kThreads) mttkrp_remap_kernel(const MttkrpArgs
     }
     if (row == a.last_row) zero_rows_group((int64_t)row + 1, out_rows);
   };
-  auto store_slot = [&](int sb, int s, int row, int prev, const float* acc) {
-    const int so = sb * 2 * NG + s;
+  auto store_slot = [&](int s, int row, int prev, const float* acc) {
     if (sub == 0) {
-      srow[so] = row;
-      sprev[so] = prev;
+      srow[s] = row;
+      sprev[s] = prev;
     }
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
       const int r = rank_of(j);
-      if (r < R) sacc[(size_t)so * R + r] = acc[j];
+      if (r < R) sacc[(size_t)s * R + r] = acc[j];
     }
   };
 
-  // ---- combine (one warp): slots of tile tt in run order, then the block's last row
-  constexpr int CC = (kMaxRank + 31) / 32;
-  auto combine = [&](int tt) {
-    const int sb = tt & 1;
-    int crow = cmeta[0], cprev = cmeta[1], emitted = cmeta[2];
-    const int ncc = (R + 31) / 32;
-    float ca[CC];
-#pragma unroll
-    for (int c = 0; c < CC; ++c) ca[c] = (c < ncc && lane + 32 * c < R) ? cacc[lane + 32 * c] : 0.f;
-
-    auto emit = [&](int row, int prev, bool first, bool last) {
-      const bool split = (first && (bi.w & BLK_HEAD_SPLIT)) || (last && (bi.w & BLK_TAIL_SPLIT));
-      if (split) {
-        float* d = a.part + ((size_t)blockIdx.x * 2 + (first ? 0 : 1)) * R;
-#pragma unroll
-        for (int c = 0; c < CC; ++c)
-          if (c < ncc && lane + 32 * c < R) d[lane + 32 * c] = ca[c];
-        return;
-      }
-      for (int64_t z = (int64_t)prev + 1; z < row; ++z)
-#pragma unroll
-        for (int c = 0; c < CC; ++c)
-          if (c < ncc && lane + 32 * c < R) out[z * R + lane + 32 * c] = 0.f;
-#pragma unroll
-      for (int c = 0; c < CC; ++c)
-        if (c < ncc && lane + 32 * c < R) out[(int64_t)row * R + lane + 32 * c] = ca[c] * sc;
-      if (row == a.last_row)
-        for (int64_t z = (int64_t)row + 1; z < out_rows; ++z)
-#pragma unroll
-          for (int c = 0; c < CC; ++c)
-            if (c < ncc && lane + 32 * c < R) out[z * R + lane + 32 * c] = 0.f;
-    };
-
-    for (int s = 0; s < 2 * NG; ++s) {
-      const int so = sb * 2 * NG + s;
-      const int row = srow[so];
-      if (row < 0) continue;
-      const float* sa = sacc + (size_t)so * R;
-      if (row == crow) {
-#pragma unroll
-        for (int c = 0; c < CC; ++c)
-          if (c < ncc && lane + 32 * c < R) ca[c] += sa[lane + 32 * c];
-      } else {
-        if (crow >= 0) {
-          emit(crow, cprev, emitted == 0, false);
-          emitted = 1;
-        }
-        const int pv = sprev[so];
-        cprev = (pv != -2) ? pv : (crow >= 0 ? crow : cprev);
-        crow = row;
-#pragma unroll
-        for (int c = 0; c < CC; ++c)
-          if (c < ncc && lane + 32 * c < R) ca[c] = sa[lane + 32 * c];
-      }
+  // carry of the warp combine: the row continuing into the next tile; its
+  // partial sum lives in shared memory (lanes over R) to keep registers for
+  // the gathers in flight
+  int crow = -1, cprev = bi.z, emitted = 0;
+  auto emit = [&](int row, int prev, bool first, bool last) {
+    const bool split = (first && (bi.w & BLK_HEAD_SPLIT)) || (last && (bi.w & BLK_TAIL_SPLIT));
+    if (split) {
+      float* d = a.part + ((size_t)wb * 2 + (first ? 0 : 1)) * R;
+      for (int r = lane; r < R; r += 32) d[r] = cacc[r];
+      return;
     }
-    if (tt == ntiles - 1) {
-      if (crow >= 0) emit(crow, cprev, emitted == 0, true);
-    } else {
-#pragma unroll
-      for (int c = 0; c < CC; ++c)
-        if (c < ncc && lane + 32 * c < R) cacc[lane + 32 * c] = ca[c];
-      __syncwarp();
-      if (lane == 0) {
-        cmeta[0] = crow;
-        cmeta[1] = cprev;
-        cmeta[2] = emitted;
-      }
-    }
+    for (int64_t z = (int64_t)prev + 1; z < row; ++z)
+      for (int r = lane; r < R; r += 32) out[z * R + r] = 0.f;
+    for (int r = lane; r < R; r += 32) out[(int64_t)row * R + r] = cacc[r] * sc;
+    if (row == a.last_row)
+      for (int64_t z = (int64_t)row + 1; z < out_rows; ++z)
+        for (int r = lane; r < R; r += 32) out[z * R + r] = 0.f;
   };
 
   int issued = min(ntiles, 2);
-  for (int t = 0; t <= ntiles; ++t) {
-    if (tid == 0 && t < ntiles) {
-      if (!mbar_wait_bounded(&mbar[t % kNBuf], (uint32_t)((t / kNBuf) & 1))) cmeta[3] = 1;
-    }
-    __syncthreads();
-    if (cmeta[3]) {
+  for (int t = 0; t < ntiles; ++t) {
+    const int st = t % kStages;
+    const bool ok = mbar_wait_bounded(&mbar[st], (uint32_t)((t / kStages) & 1));
+    if (!__all_sync(0xffffffffu, ok)) {
       // a bulk copy did not complete in time: record it, wait (bounded) for
-      // the copies still in flight, and leave without touching the outputs
-      if (tid == 0) {
+      // the copies still in flight, and leave without writing anything else
+      if (lane == 0) {
         atomicOr(a.err, 1);
         for (int q = t; q < issued; ++q)
-          (void)mbar_wait_bounded(&mbar[q % kNBuf], (uint32_t)((q / kNBuf) & 1));
+          (void)mbar_wait_bounded(&mbar[q % kStages], (uint32_t)((q / kStages) & 1));
       }
       return;
     }
-    if (tid == 0 && t + 2 < ntiles) {
+    // the stage of tile t+2 held tile t-1, whose readers passed the last __syncwarp
+    if (lane == 0 && t + 2 < ntiles) {
       issue(t + 2);
       issued = t + 3;
     }
-    if (t >= 1 && warp == (t - 1) % (kThreads / 32)) combine(t - 1);
-    if (t == ntiles) break;
-
-    // ---- tile t
-    const int buf = t % kNBuf, sb = t & 1;
-    const int tlo = lo + t * tile;
-    const int n = min(tile, hi - tlo);
-    const uint8_t* eb = ebuf + (size_t)buf * tile * es;
+    const int tlo = lo + t * TW;
+    const int n = min(TW, hi - tlo);
+    const uint8_t* eb = ebuf + (size_t)st * TW * es;
 
     if (remap) {  // Algorithm 3: every element to its place in the next mode's order
-      const int32_t* np = npbuf + buf * (tile + 8) + (tlo & 3);
+      const int32_t* np = npbuf + st * (TW + 8) + (tlo & 3);
       const int nv = es / 16;
-      for (int i = tid; i < n * nv; i += kThreads) {
+      for (int i = lane; i < n * nv; i += 32) {
         const int e = i / nv, c = i - e * nv;
         const uint4 v = reinterpret_cast<const uint4*>(eb + (size_t)e * es)[c];
         reinterpret_cast<uint4*>(a.elems_out + (size_t)np[e] * es)[c] = v;
@@ -434,106 +228,132 @@ __global__ void __launch_bounds__(kThreads) mttkrp_remap_kernel(const MttkrpArgs
     }
 
     // Algorithm 2 over this group's run [a0, b0) of the tile
-    const int a0 = gi * K, b0 = min(a0 + K, n);
+    const int a0 = gw * K, b0 = min(a0 + K, n);
     if (a0 >= b0) {
       if (sub == 0) {
-        srow[sb * 2 * NG + 2 * gi] = -1;
-        srow[sb * 2 * NG + 2 * gi + 1] = -1;
+        srow[2 * gw] = -1;
+        srow[2 * gw + 1] = -1;
       }
-      continue;
-    }
-    float acc[NV];
+    } else {
+      float acc[NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) acc[j] = 0.f;
-    int cur = reinterpret_cast<const int*>(eb + (size_t)a0 * es)[mode];
-    bool head = true;
-    int prev_in_run = -1;
-    for (int e = a0; e < b0; e += U) {
-      float prod[U][NV];
-      int rows[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (e + u < b0) {
-          const int* el = reinterpret_cast<const int*>(eb + (size_t)(e + u) * es);
-          rows[u] = el[mode];
-          const float v = __int_as_float(el[N]);
-#pragma unroll
-          for (int j = 0; j < NV; ++j) prod[u][j] = v;
-        }
-      }
-      for (int k = 0; k < N; ++k) {
-        if (k == mode) continue;
-        const void* Ak = a.factors[k];
+      for (int j = 0; j < NV; ++j) acc[j] = 0.f;
+      int cur = reinterpret_cast<const int*>(eb + (size_t)a0 * es)[mode];
+      bool head = true;
+      int prev_in_run = -1;
+      auto batch = [&](int e, int nb) {
+        float prod[U][NV];
+        int rows[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          if (e + u < b0) {
-            const int64_t idx = reinterpret_cast<const int*>(eb + (size_t)(e + u) * es)[k];
-            float x[NV];
-            if constexpr (VW > 1) {
-              if (sub * VW < R) {
-                Slice<T, VW>::load(Ak, idx, R, sub, x);
+          if (u < nb) {
+            const int* el = reinterpret_cast<const int*>(eb + (size_t)(e + u) * es);
+            rows[u] = el[mode];
+            const float v = __int_as_float(el[N]);
+#pragma unroll
+            for (int j = 0; j < NV; ++j) prod[u][j] = v;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < (NT > 0 ? NT : kMaxModes); ++k) {
+          if (k >= N) break;
+          if (k == mode) continue;
+          const void* Ak = a.factors[k];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (u < nb) {
+              const int64_t ix = reinterpret_cast<const int*>(eb + (size_t)(e + u) * es)[k];
+              float x[NV];
+              if constexpr (VW > 1) {
+                if (sub * VW < R) {
+                  Slice<T, VW>::load(Ak, ix, R, sub, x);
+                } else {
+#pragma unroll
+                  for (int j = 0; j < NV; ++j) x[j] = 0.f;
+                }
               } else {
 #pragma unroll
-                for (int j = 0; j < NV; ++j) x[j] = 0.f;
+                for (int j = 0; j < NV; ++j) {
+                  const int r = rank_of(j);
+                  x[j] = (r < R) ? load_scalar<T>(Ak, ix * R + r) : 0.f;
+                }
               }
-            } else {
 #pragma unroll
-              for (int j = 0; j < NV; ++j) {
-                const int r = rank_of(j);
-                x[j] = (r < R) ? load_scalar<T>(Ak, idx * R + r) : 0.f;
-              }
+              for (int j = 0; j < NV; ++j) prod[u][j] *= x[j];
             }
-#pragma unroll
-            for (int j = 0; j < NV; ++j) prod[u][j] *= x[j];
           }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (e + u < b0) {
-          if (rows[u] != cur) {
-            if (head) {
-              store_slot(sb, 2 * gi, cur, -2, acc);
-              head = false;
-            } else {
-              write_row_group(cur, acc, prev_in_run);
+        for (int u = 0; u < U; ++u) {
+          if (u < nb) {
+            if (rows[u] != cur) {
+              if (head) {
+                store_slot(2 * gw, cur, -2, acc);
+                head = false;
+              } else {
+                write_row_group(cur, acc, prev_in_run);
+              }
+              prev_in_run = cur;
+              cur = rows[u];
+#pragma unroll
+              for (int j = 0; j < NV; ++j) acc[j] = 0.f;
             }
-            prev_in_run = cur;
-            cur = rows[u];
 #pragma unroll
-            for (int j = 0; j < NV; ++j) acc[j] = 0.f;
+            for (int j = 0; j < NV; ++j) acc[j] += prod[u][j];
           }
-#pragma unroll
-          for (int j = 0; j < NV; ++j) acc[j] += prod[u][j];
         }
+      };
+      int e = a0;
+      for (; e + U <= b0; e += U) batch(e, U);
+      for (; e < b0; ++e) batch(e, 1);
+      if (head) {
+        store_slot(2 * gw, cur, -2, acc);
+        if (sub == 0) srow[2 * gw + 1] = -1;
+      } else {
+        store_slot(2 * gw + 1, cur, prev_in_run, acc);
       }
     }
-    if (head) {
-      store_slot(sb, 2 * gi, cur, -2, acc);
-      if (sub == 0) srow[sb * 2 * NG + 2 * gi + 1] = -1;
-    } else {
-      store_slot(sb, 2 * gi + 1, cur, prev_in_run, acc);
+    __syncwarp();
+
+    // warp combine: run-boundary rows of this tile in run order
+    for (int s = 0; s < 2 * G; ++s) {
+      const int row = srow[s];
+      if (row < 0) continue;
+      const float* sa = sacc + (size_t)s * R;
+      if (row == crow) {
+        for (int r = lane; r < R; r += 32) cacc[r] += sa[r];
+      } else {
+        if (crow >= 0) {
+          emit(crow, cprev, emitted == 0, false);
+          emitted = 1;
+        }
+        const int pv = sprev[s];
+        cprev = (pv != -2) ? pv : (crow >= 0 ? crow : cprev);
+        crow = row;
+        for (int r = lane; r < R; r += 32) cacc[r] = sa[r];
+      }
     }
+    __syncwarp();
   }
+  if (crow >= 0) emit(crow, cprev, emitted == 0, true);
 }
 
-// ------------------------------------------------------------ launcher
-
-template <int NT, typename T, int VW, int RC>
-int launch_variant(const MttkrpArgs& a, int L, cudaStream_t s) {
-  const int NG = (kThreads / 32) * (32 / L);
-  const SmemLayout lay = smem_layout(a.es, a.tile, a.R, NG);
-  auto kfn = mttkrp_remap_kernel<NT, T, VW, RC>;
-  static int configured = 0;  // per instantiation: raise the dynamic smem limit once
-  if (configured < (int)lay.total) {
+template <int NT, typename T, int VW, int RC, int U>
+int launch_warp_kernel(const MttkrpArgs& a, int L, cudaStream_t s) {
+  const int G = 32 / L;
+  const size_t smem = (size_t)kWarps * warp_layout(a.es, a.tile, a.R, G).total;
+  auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U>;
+  static size_t configured = 0;  // per instantiation: raise the dynamic smem limit once
+  if (configured < smem) {
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max<size_t>(lay.total, 48 * 1024));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mttkrp)");
-    configured = (int)std::max<size_t>(lay.total, 48 * 1024);
+                                         (int)std::max<size_t>(smem, 48 * 1024));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mttkrp_warp)");
+    configured = std::max<size_t>(smem, 48 * 1024);
   }
-  kfn<<<a.nblk, kThreads, lay.total, s>>>(a, L);
+  const int grid = (a.nblk + kWarps - 1) / kWarps;
+  kfn<<<grid, kThreads, smem, s>>>(a, L);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "mttkrp_remap_kernel launch");
+  if (e != cudaSuccess) return cuda_fail(e, "mttkrp_warp_kernel launch");
   return SPM_OK;
 }
 

@@ -95,16 +95,24 @@ static void stable_sort_by(const int32_t* key, int64_t dim, std::vector<int32_t>
   }
 }
 
-int default_nblk(int64_t nnz, int num_sms) {
+int default_nblk(int64_t nnz, int num_sms, int variant) {
   if (nnz <= 0) return 1;
-  // about 32K nonzeros per block for large tensors, at least 4 blocks per SM
-  // while each keeps >= 256 nonzeros
-  int64_t big = (nnz + 32767) / 32768;
-  int64_t small = std::min<int64_t>((int64_t)num_sms * 4, (nnz + 255) / 256);
-  int64_t nb = std::max<int64_t>(big, small);
-  nb = std::max<int64_t>(1, std::min<int64_t>(nb, 1 << 20));
-  return (int)nb;
+  int64_t nb;
+  if (variant == 0) {
+    // warp blocks: about four waves of 24 resident warps per SM, each block
+    // >= 256 nonzeros, and never more than 16K nonzeros per block
+    nb = std::max<int64_t>(std::min<int64_t>((int64_t)num_sms * 24 * 4, (nnz + 255) / 256),
+                           (nnz + 16383) / 16384);
+  } else {
+    // CTA blocks: about 32K nonzeros each, at least 4 per SM while each keeps
+    // >= 256 nonzeros
+    nb = std::max<int64_t>((nnz + 32767) / 32768,
+                           std::min<int64_t>((int64_t)num_sms * 4, (nnz + 255) / 256));
+  }
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nb, 1 << 22));
 }
+
+int default_tile(int es) { return es <= 16 ? 128 : (es <= 32 ? 64 : 32); }
 
 // Position -> index of the nonempty row holding it (ustart ascending, size nu+1).
 static inline int64_t row_index_of(const std::vector<int64_t>& ustart, int64_t pos) {
@@ -318,7 +326,7 @@ int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int
   // partitions
   p->mh.assign((size_t)N, ModeHost());
   for (int n = 0; n < N; ++n) {
-    int nb = nblk_opt > 0 ? nblk_opt : default_nblk(nnz, p->num_sms);
+    int nb = nblk_opt > 0 ? nblk_opt : default_nblk(nnz, p->num_sms, p->variant);
     int st = partition_mode(p, n, nb, &p->mh[(size_t)n]);
     if (st != SPM_OK) return st;
   }
