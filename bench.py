@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--variant", type=int, default=0,
                     help="0 warp blocks with staged tiles, 1 CTA blocks with direct runs")
+    ap.add_argument("--unroll", type=int, default=0)
+    ap.add_argument("--hints", type=int, default=0, help="-1 none, 0 default, 1..3 bits")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -277,7 +279,7 @@ def main():
     torch.cuda.empty_cache()
     t0 = time.perf_counter()
     plan = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, nblk=args.nblk, tile=args.tile,
-                variant=args.variant)
+                variant=args.variant, unroll=args.unroll, cache_hints=args.hints)
     plan_s = time.perf_counter() - t0
     info = plan.info()
     outs = [torch.empty(d, R, device=dev) for d in spec.dims]
@@ -370,6 +372,7 @@ def main():
                        "factor_dtype": args.dtype, "nblk": info["nblk"], "tile": info["tile"],
                        "kernel_form": ["warp blocks, bulk-async staged tiles",
                                        "CTA blocks, direct runs"][args.variant],
+                       "unroll": args.unroll or 8, "cache_hints": args.hints,
                        "l2": "inputs larger than L2 (element stream "
                              f"{nnz * info['elem_bytes'] / 1e9:.2f} GB per mode)",
                        "parallelism": f"replicas x{world}"},

@@ -69,6 +69,10 @@ typedef struct {
   int variant;      /* fused kernel form: 0 = one warp per block, tiles staged in
                        shared memory by bulk async copies (default); 1 = one CTA
                        per block, each lane group streams one contiguous run     */
+  int unroll;       /* nonzeros in flight per lane group in form 0: 0 (= 8), 4, 8 */
+  int cache_hints;  /* form 0 L2 policy: -1 = none, 0 = default (= 3); bit0: the
+                       nonzero stream, remap ids and remapped copy evict first;
+                       bit1: factor rows evict last                               */
   void* stream;     /* cudaStream_t for all work; NULL = default stream           */
 } spmttkrp_opts_t;
 

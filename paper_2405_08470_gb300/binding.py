@@ -42,6 +42,7 @@ class Opts(ctypes.Structure):
                 ("nblk", ctypes.c_int), ("tile", ctypes.c_int),
                 ("max_bytes", ctypes.c_size_t), ("checks", ctypes.c_int),
                 ("host_only", ctypes.c_int), ("variant", ctypes.c_int),
+                ("unroll", ctypes.c_int), ("cache_hints", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -115,7 +116,8 @@ class Plan:
 
     def __init__(self, coo, vals, dims: Sequence[int], rank: int, dtype: str = "f32",
                  nblk: int = 0, tile: int = 0, max_bytes: int = 0, checks: bool = False,
-                 host_only: bool = False, stream=None, variant: int = 0):
+                 host_only: bool = False, stream=None, variant: int = 0, unroll: int = 0,
+                 cache_hints: int = 0):
         L = lib()
         coo = np.ascontiguousarray(np.asarray(coo.cpu() if hasattr(coo, "cpu") else coo,
                                               dtype=np.int64))
@@ -132,6 +134,7 @@ class Plan:
         o.nblk, o.tile, o.max_bytes = int(nblk), int(tile), int(max_bytes)
         o.checks, o.host_only = int(bool(checks)), int(bool(host_only))
         o.variant = int(variant)
+        o.unroll, o.cache_hints = int(unroll), int(cache_hints)
         o.stream = None if host_only else _stream_ptr(stream)
         d = np.asarray(self.dims, dtype=np.int64)
         h = ctypes.c_void_p()

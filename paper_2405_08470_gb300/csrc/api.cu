@@ -144,6 +144,8 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   a.scale = scale;
   a.dtype = p->dtype;
   a.variant = p->variant;
+  a.hints = p->hints;
+  a.unroll = p->unroll;
   int st = launch_mttkrp(a, p->stream);
   if (st) return st;
   return launch_fixup(p->d_part, d.splits, d.nsplit, out, a.out_rows, p->R, scale, p->stream);
@@ -216,6 +218,10 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     return fail(SPM_ERR_INVALID_ARG, "tile must be 0, 32, 64, 128 or 256");
   if (o.nblk < 0) return fail(SPM_ERR_INVALID_ARG, "nblk must be >= 0");
   if (o.variant != 0 && o.variant != 1) return fail(SPM_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (o.unroll != 0 && o.unroll != 4 && o.unroll != 8)
+    return fail(SPM_ERR_INVALID_ARG, "unroll must be 0, 4 or 8");
+  if (o.cache_hints < -1 || o.cache_hints > 3)
+    return fail(SPM_ERR_INVALID_ARG, "cache_hints must be in [-1, 3]");
 
   spmttkrp_plan* p = new (std::nothrow) spmttkrp_plan();
   if (!p) return fail(SPM_ERR_OOM, "host allocation failed");
@@ -224,6 +230,8 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->nnz = nnz;
   p->dtype = o.factor_dtype;
   p->variant = o.variant;
+  p->unroll = o.unroll ? o.unroll : 8;
+  p->hints = o.cache_hints == 0 ? 3 : (o.cache_hints < 0 ? 0 : o.cache_hints);
   p->checks = o.checks;
   p->host_only = o.host_only;
   p->max_bytes = o.max_bytes;

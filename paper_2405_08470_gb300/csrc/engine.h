@@ -60,6 +60,8 @@ struct GraphCache {
 struct spmttkrp_plan {
   int N = 0, R = 0, dtype = 0, tile = 512, checks = 0, host_only = 0;
   int variant = 0;  // fused-kernel form: 0 = warp blocks, staged tiles; 1 = CTA blocks, direct runs
+  int hints = 3;    // L2 cache policy bits of the fused kernel (see MttkrpArgs)
+  int unroll = 0;   // nonzeros in flight per lane group of the warp-block form
   int64_t nnz = 0;
   int es = 16;  // element stride in bytes: {int32 idx[N]; float val}, rounded up to 16
   std::vector<int64_t> dims;
@@ -136,6 +138,8 @@ struct MttkrpArgs {
   const float* scale;      // device scalar multiplier or null
   int dtype;
   int variant;             // 0 = warp blocks, staged tiles; 1 = CTA blocks, direct runs
+  int hints;               // bit0: streams evict_first in L2; bit1: factor rows evict_last
+  int unroll;              // nonzeros in flight per lane group (4 or 8; 0 = default)
 };
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
 int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* out,

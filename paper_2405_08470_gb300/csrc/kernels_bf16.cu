@@ -27,11 +27,13 @@ int launch_mttkrp_bf16(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
   if (a.variant == 1) return launch_direct_bfloat16(a, c, s);
   if (c.vec) {
     switch (a.nmodes) {
-      case 3: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
-      case 4: return launch_warp_kernel<4, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
-      case 5: return launch_warp_kernel<5, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
-      case 6: return launch_warp_kernel<6, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
-      default: return launch_warp_kernel<0, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
+      case 3:
+        return a.unroll == 4 ? launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4>(a, c.L, s)
+                             : launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
+      case 4: return launch_warp_kernel<4, __nv_bfloat16, 8, 1, 4>(a, c.L, s);
+      case 5: return launch_warp_kernel<5, __nv_bfloat16, 8, 1, 4>(a, c.L, s);
+      case 6: return launch_warp_kernel<6, __nv_bfloat16, 8, 1, 4>(a, c.L, s);
+      default: return launch_warp_kernel<0, __nv_bfloat16, 8, 1, 4>(a, c.L, s);
     }
   }
   switch (c.RC) {

@@ -26,7 +26,9 @@ int launch_mttkrp_f32(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
   if (a.variant == 1) return launch_direct_float(a, c, s);
   if (c.vec) {
     switch (a.nmodes) {
-      case 3: return launch_warp_kernel<3, float, 4, 1, 8>(a, c.L, s);
+      case 3:
+        return a.unroll == 4 ? launch_warp_kernel<3, float, 4, 1, 4>(a, c.L, s)
+                             : launch_warp_kernel<3, float, 4, 1, 8>(a, c.L, s);
       case 4: return launch_warp_kernel<4, float, 4, 1, 8>(a, c.L, s);
       case 5: return launch_warp_kernel<5, float, 4, 1, 8>(a, c.L, s);
       case 6: return launch_warp_kernel<6, float, 4, 1, 8>(a, c.L, s);

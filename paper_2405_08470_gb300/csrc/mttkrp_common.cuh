@@ -84,6 +84,45 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// 1D bulk async copy with an L2 cache policy (e.g. evict_first for streams).
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+// L2 cache policies: 0 = evict_normal, 1 = evict_first, 2 = evict_last.
+__device__ __forceinline__ uint64_t make_policy(int kind) {
+  uint64_t p;
+  if (kind == 1)
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  else if (kind == 2)
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  else
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// 16-byte global store with an L2 cache policy, not allocated in L1.
+__device__ __forceinline__ void st_hint_v4(void* ptr, uint4 v, uint64_t policy) {
+  asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(
+                   ptr),
+               "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(policy)
+               : "memory");
+}
+
+// 16-byte read-only global load with an L2 cache policy.
+__device__ __forceinline__ uint4 ld_nc_hint_v4(const void* ptr, uint64_t policy) {
+  uint4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(ptr), "l"(policy));
+  return v;
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -124,20 +163,40 @@ struct Slice<float, 4> {
     x[2] = v.z;
     x[3] = v.w;
   }
+  __device__ __forceinline__ static void load_hint(const void* base, int64_t row, int R, int sub,
+                                                   uint64_t pol, float* x) {
+    const uint4 v = ld_nc_hint_v4(
+        reinterpret_cast<const float4*>(static_cast<const float*>(base) + row * R) + sub, pol);
+    x[0] = __uint_as_float(v.x);
+    x[1] = __uint_as_float(v.y);
+    x[2] = __uint_as_float(v.z);
+    x[3] = __uint_as_float(v.w);
+  }
 };
 
 template <>
 struct Slice<__nv_bfloat16, 8> {
-  __device__ __forceinline__ static void load(const void* base, int64_t row, int R, int sub,
-                                              float* x) {
-    const uint4 v = __ldg(
-        reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * R) + sub);
+  __device__ __forceinline__ static void unpack(uint4 v, float* x) {
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       x[2 * j] = __uint_as_float(w[j] << 16);
       x[2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
     }
+  }
+  __device__ __forceinline__ static void load(const void* base, int64_t row, int R, int sub,
+                                              float* x) {
+    unpack(__ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * R) +
+                 sub),
+           x);
+  }
+  __device__ __forceinline__ static void load_hint(const void* base, int64_t row, int R, int sub,
+                                                   uint64_t pol, float* x) {
+    unpack(ld_nc_hint_v4(
+               reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(base) + row * R) +
+                   sub,
+               pol),
+           x);
   }
 };
 

@@ -66,7 +66,8 @@ __host__ __device__ inline WarpLayout warp_layout(int es, int tw, int R, int G) 
 __host__ __device__ inline int warp_tile(int es) { return es <= 16 ? 128 : (es <= 32 ? 64 : 32); }
 
 template <int NT, typename T, int VW, int RC, int U>
-__global__ void __launch_bounds__(kThreads) mttkrp_warp_kernel(const MttkrpArgs a, const int L) {
+__global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1) ? 3 : 2)) mttkrp_warp_kernel(const MttkrpArgs a,
+                                                                            const int L) {
   constexpr int NV = VW * RC;
   const int N = NT > 0 ? NT : a.nmodes;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -95,6 +96,10 @@ __global__ void __launch_bounds__(kThreads) mttkrp_warp_kernel(const MttkrpArgs 
   const float sc = a.scale ? __ldg(a.scale) : 1.0f;
   const int64_t out_rows = a.out_rows;
   float* __restrict__ out = a.out;
+  // L2 policies: the element stream, remap ids and remapped copy are touched
+  // once per mode (evict first); factor rows are reused (evict last)
+  const uint64_t pol_stream = make_policy((a.hints & 1) ? 1 : 0);
+  const uint64_t pol_factor = make_policy((a.hints & 2) ? 2 : 0);
 
   auto issue = [&](int t) {  // lane 0 only
     const int st = t % kStages;
@@ -109,8 +114,10 @@ __global__ void __launch_bounds__(kThreads) mttkrp_warp_kernel(const MttkrpArgs 
     }
     fence_proxy_async_smem();
     mbar_expect_tx(&mbar[st], ebytes + npbytes);
-    bulk_g2s(ebuf + (size_t)st * TW * es, a.elems_in + (size_t)tlo * es, ebytes, &mbar[st]);
-    if (remap) bulk_g2s(npbuf + st * (TW + 8), a.next_pos + np0, npbytes, &mbar[st]);
+    bulk_g2s_hint(ebuf + (size_t)st * TW * es, a.elems_in + (size_t)tlo * es, ebytes, &mbar[st],
+                  pol_stream);
+    if (remap)
+      bulk_g2s_hint(npbuf + st * (TW + 8), a.next_pos + np0, npbytes, &mbar[st], pol_stream);
   };
 
   if (lane == 0) {
@@ -223,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) mttkrp_warp_kernel(const MttkrpArgs 
       for (int i = lane; i < n * nv; i += 32) {
         const int e = i / nv, c = i - e * nv;
         const uint4 v = reinterpret_cast<const uint4*>(eb + (size_t)e * es)[c];
-        reinterpret_cast<uint4*>(a.elems_out + (size_t)np[e] * es)[c] = v;
+        st_hint_v4(reinterpret_cast<uint4*>(a.elems_out + (size_t)np[e] * es) + c, v, pol_stream);
       }
     }
 
@@ -243,15 +250,15 @@ __global__ void __launch_bounds__(kThreads) mttkrp_warp_kernel(const MttkrpArgs 
       int prev_in_run = -1;
       auto batch = [&](int e, int nb) {
         float prod[U][NV];
+        float vals[U];
         int rows[U];
+        bool first_k = true;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (u < nb) {
             const int* el = reinterpret_cast<const int*>(eb + (size_t)(e + u) * es);
             rows[u] = el[mode];
-            const float v = __int_as_float(el[N]);
-#pragma unroll
-            for (int j = 0; j < NV; ++j) prod[u][j] = v;
+            vals[u] = __int_as_float(el[N]);
           }
         }
 #pragma unroll
@@ -266,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) mttkrp_warp_kernel(const MttkrpArgs 
               float x[NV];
               if constexpr (VW > 1) {
                 if (sub * VW < R) {
-                  Slice<T, VW>::load(Ak, ix, R, sub, x);
+                  Slice<T, VW>::load_hint(Ak, ix, R, sub, pol_factor, x);
                 } else {
 #pragma unroll
                   for (int j = 0; j < NV; ++j) x[j] = 0.f;
@@ -279,9 +286,10 @@ __global__ void __launch_bounds__(kThreads) mttkrp_warp_kernel(const MttkrpArgs 
                 }
               }
 #pragma unroll
-              for (int j = 0; j < NV; ++j) prod[u][j] *= x[j];
+              for (int j = 0; j < NV; ++j) prod[u][j] = first_k ? x[j] : prod[u][j] * x[j];
             }
           }
+          first_k = false;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -299,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) mttkrp_warp_kernel(const MttkrpArgs 
               for (int j = 0; j < NV; ++j) acc[j] = 0.f;
             }
 #pragma unroll
-            for (int j = 0; j < NV; ++j) acc[j] += prod[u][j];
+            for (int j = 0; j < NV; ++j) acc[j] = fmaf(prod[u][j], vals[u], acc[j]);
           }
         }
       };

@@ -29,12 +29,12 @@ def built():
 
 
 def run_all_modes(coo, vals, dims, R, dtype="f32", nblk=0, tile=0, seed=3, graph=False,
-                  check_order=True, scale=1.0):
+                  check_order=True, scale=1.0, variant=0):
     c, v = coo.numpy(), vals.numpy()
     F = synth.make_factors(dims, R, seed=seed, scale=scale)
     tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
     Fd = [f.to(tdt).cuda() for f in F]
-    p = Plan(c, v, dims, R, dtype=dtype, nblk=nblk, tile=tile, checks=True)
+    p = Plan(c, v, dims, R, dtype=dtype, nblk=nblk, tile=tile, checks=True, variant=variant)
     N = len(dims)
     outs = [torch.full((d, R), float("nan"), device="cuda") for d in dims]
     for n in range(N):
@@ -88,10 +88,12 @@ def test_c1_workload_all_modes():
 
 @pytest.mark.parametrize("R", [1, 3, 4, 12, 17, 33, 100, 256])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_odd_ranks_scalar_and_masked_paths(R, dtype):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_odd_ranks_scalar_and_masked_paths(R, dtype, variant):
     dims = (40, 30, 20)
     coo, vals = synth.make_coo(dims, 2500, (1.1, 0.0, 1.1), seed=R)
-    p, got, F, Fh = run_all_modes(coo, vals, dims, R, dtype=dtype, nblk=13, check_order=False)
+    p, got, F, Fh = run_all_modes(coo, vals, dims, R, dtype=dtype, nblk=13, check_order=False,
+                                  variant=variant)
     c, v = coo.numpy(), vals.numpy()
     for n in range(3):
         assert np.all(np.isfinite(got[n]))
@@ -110,12 +112,14 @@ def test_generic_mode_counts(N):
     p.close()
 
 
-@pytest.mark.parametrize("tile,nblk", [(256, 1), (512, 3), (1024, 7), (256, 97), (512, 0)])
-def test_tiles_blocks_and_ragged_tails(tile, nblk):
+@pytest.mark.parametrize("tile,nblk,variant", [(32, 1, 0), (64, 3, 0), (128, 7, 0), (256, 97, 0),
+                                               (128, 0, 0), (128, 1, 1), (128, 5, 1),
+                                               (128, 0, 1)])
+def test_tiles_blocks_and_ragged_tails(tile, nblk, variant):
     # 7,777 nonzeros: not a multiple of any tile; blocks span several tiles
     dims = (500, 80, 60)
     coo, vals = synth.make_coo(dims, 7777, (1.2, 1.1, 0.0), seed=tile + nblk)
-    p, got, F, Fh = run_all_modes(coo, vals, dims, 32, nblk=nblk, tile=tile)
+    p, got, F, Fh = run_all_modes(coo, vals, dims, 32, nblk=nblk, tile=tile, variant=variant)
     c, v = coo.numpy(), vals.numpy()
     for n in range(3):
         assert O.relerr(got[n], O.mttkrp(c, v, dims, Fh, n)) <= F32_TOL
