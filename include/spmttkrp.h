@@ -202,6 +202,36 @@ enum {
 int spmttkrp_plan_query(spmttkrp_plan_t plan, int what, int mode, void* host_dst,
                         size_t bytes);
 
+/*
+ * Mode-n spMTTKRP (and, optionally, the remap into mode n+1 order) for callers
+ * that cannot allocate device memory: code running where cudaMalloc is not
+ * allowed or not possible (an allocator-free region of a host framework, a
+ * process whose device memory is owned by another pool).  Such callers cannot
+ * create a plan, so everything is passed in; the call allocates nothing.  The
+ * paper has no counterpart: this is an engineering entry point.
+ *   elems      device, nnz nonzeros in mode-`mode` canonical order, each
+ *              {int32 idx[nmodes]; float val} padded with zeros to a stride of
+ *              (4*nmodes+4) rounded up to 16 bytes (the plan's layout).
+ *   dims       host, int64 [nmodes];  factors: host array of device pointers.
+ *   out        device, float [dims[mode]][rank], fully overwritten.
+ *   elems_out, next_pos  both NULL (no remap) or both device: element p is
+ *              written to elems_out[next_pos[p]] (int32 [nnz]).
+ *   nblk       blocks of the even split (0 = automatic), at most 4096.
+ *   stream     cudaStream_t (NULL = default stream); the call is asynchronous.
+ * Scratch (block descriptors, split-row table, split-row partial sums) lives in
+ * one static device array of 8.25 MiB that every device using the library
+ * keeps until the process exits: at most 4096 blocks and rank <= 256; larger
+ * requests return SPM_ERR_UNSUPPORTED.  The first call on a device looks up
+ * that array's device address; make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Every scratch entry a call reads is written earlier in the same call.
+ */
+int spmttkrp_compute_noalloc(const void* elems, int64_t nnz, int nmodes, int mode,
+                             const int64_t* dims, int rank, int factor_dtype,
+                             const void* const* factors, float* out, void* elems_out,
+                             const int32_t* next_pos, int nblk, void* stream);
+
 /* Synchronizes, returns SPM_OK or the first recorded device-side error
  * (e.g. SPM_ERR_TIMEOUT) and clears it. */
 int spmttkrp_device_status(spmttkrp_plan_t plan);
