@@ -217,7 +217,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   if (o.tile != 0 && o.tile != 32 && o.tile != 64 && o.tile != 128 && o.tile != 256)
     return fail(SPM_ERR_INVALID_ARG, "tile must be 0, 32, 64, 128 or 256");
   if (o.nblk < 0) return fail(SPM_ERR_INVALID_ARG, "nblk must be >= 0");
-  if (o.variant != 0 && o.variant != 1) return fail(SPM_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (o.variant < 0 || o.variant > 1) return fail(SPM_ERR_INVALID_ARG, "variant must be 0 or 1");
   if (o.unroll != 0 && o.unroll != 4 && o.unroll != 8)
     return fail(SPM_ERR_INVALID_ARG, "unroll must be 0, 4 or 8");
   if (o.cache_hints < -1 || o.cache_hints > 3)

@@ -279,8 +279,8 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   struct Cand {
     int nps, tile, variant;
   };
-  // blocks per SM: warp blocks (form 0) in multiples of 24 resident warps,
-  // CTA blocks (form 1) in multiples of 4
+  // blocks per SM: warp blocks (form 0) in multiples of 24 resident
+  // warps, CTA blocks (form 1) in multiples of 4
   std::vector<Cand> cands;
   for (int n : {24, 48, 96, 192}) {
     if ((int64_t)n * p->num_sms * 128 > p->nnz && n > 24) continue;

@@ -59,7 +59,7 @@ struct GraphCache {
 
 struct spmttkrp_plan {
   int N = 0, R = 0, dtype = 0, tile = 512, checks = 0, host_only = 0;
-  int variant = 0;  // fused-kernel form: 0 = warp blocks, staged tiles; 1 = CTA blocks, direct runs
+  int variant = 0;  // fused-kernel form (see MttkrpArgs::variant)
   int hints = 3;    // L2 cache policy bits of the fused kernel (see MttkrpArgs)
   int unroll = 0;   // nonzeros in flight per lane group of the warp-block form
   int64_t nnz = 0;

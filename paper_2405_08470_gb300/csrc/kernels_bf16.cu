@@ -1,5 +1,5 @@
 // kernels_bf16.cu - BF16-factor instantiations of the fused spMTTKRP + remap
-// kernel (factor rows stored in BF16, products and sums in FP32).
+// kernels (factor rows stored in BF16, products and sums in FP32).
 #include "mttkrp_direct.cuh"
 #include "mttkrp_kernel.cuh"
 
@@ -28,8 +28,18 @@ int launch_mttkrp_bf16(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
   if (c.vec) {
     switch (a.nmodes) {
       case 3:
-        return a.unroll == 4 ? launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4>(a, c.L, s)
-                             : launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8>(a, c.L, s);
+        if (a.unroll == 4) {
+          switch (a.mode) {
+            case 0: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 0>(a, c.L, s);
+            case 1: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 1>(a, c.L, s);
+            default: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 2>(a, c.L, s);
+          }
+        }
+        switch (a.mode) {
+          case 0: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8, 0>(a, c.L, s);
+          case 1: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8, 1>(a, c.L, s);
+          default: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8, 2>(a, c.L, s);
+        }
       case 4: return launch_warp_kernel<4, __nv_bfloat16, 8, 1, 4>(a, c.L, s);
       case 5: return launch_warp_kernel<5, __nv_bfloat16, 8, 1, 4>(a, c.L, s);
       case 6: return launch_warp_kernel<6, __nv_bfloat16, 8, 1, 4>(a, c.L, s);

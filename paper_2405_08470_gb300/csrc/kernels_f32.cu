@@ -1,4 +1,4 @@
-// kernels_f32.cu - FP32-factor instantiations of the fused spMTTKRP + remap kernel.
+// kernels_f32.cu - FP32-factor instantiations of the fused spMTTKRP + remap kernels.
 #include "mttkrp_direct.cuh"
 #include "mttkrp_kernel.cuh"
 
@@ -27,12 +27,22 @@ int launch_mttkrp_f32(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
   if (c.vec) {
     switch (a.nmodes) {
       case 3:
-        return a.unroll == 4 ? launch_warp_kernel<3, float, 4, 1, 4>(a, c.L, s)
-                             : launch_warp_kernel<3, float, 4, 1, 8>(a, c.L, s);
-      case 4: return launch_warp_kernel<4, float, 4, 1, 8>(a, c.L, s);
-      case 5: return launch_warp_kernel<5, float, 4, 1, 8>(a, c.L, s);
-      case 6: return launch_warp_kernel<6, float, 4, 1, 8>(a, c.L, s);
-      default: return launch_warp_kernel<0, float, 4, 1, 8>(a, c.L, s);
+        if (a.unroll == 4) {
+          switch (a.mode) {
+            case 0: return launch_warp_kernel<3, float, 4, 1, 4, 0>(a, c.L, s);
+            case 1: return launch_warp_kernel<3, float, 4, 1, 4, 1>(a, c.L, s);
+            default: return launch_warp_kernel<3, float, 4, 1, 4, 2>(a, c.L, s);
+          }
+        }
+        switch (a.mode) {
+          case 0: return launch_warp_kernel<3, float, 4, 1, 8, 0>(a, c.L, s);
+          case 1: return launch_warp_kernel<3, float, 4, 1, 8, 1>(a, c.L, s);
+          default: return launch_warp_kernel<3, float, 4, 1, 8, 2>(a, c.L, s);
+        }
+      case 4: return launch_warp_kernel<4, float, 4, 1, 4>(a, c.L, s);
+      case 5: return launch_warp_kernel<5, float, 4, 1, 4>(a, c.L, s);
+      case 6: return launch_warp_kernel<6, float, 4, 1, 4>(a, c.L, s);
+      default: return launch_warp_kernel<0, float, 4, 1, 4>(a, c.L, s);
     }
   }
   switch (c.RC) {

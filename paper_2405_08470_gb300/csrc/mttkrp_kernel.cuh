@@ -65,14 +65,70 @@ __host__ __device__ inline WarpLayout warp_layout(int es, int tw, int R, int G) 
 // Default nonzeros per warp tile: small enough that three CTAs of 8 warps fit an SM.
 __host__ __device__ inline int warp_tile(int es) { return es <= 16 ? 128 : (es <= 32 ? 64 : 32); }
 
-template <int NT, typename T, int VW, int RC, int U>
-__global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1) ? 3 : 2)) mttkrp_warp_kernel(const MttkrpArgs a,
-                                                                            const int L) {
+// Registers a gathered factor-row slice lands in before it is used: one
+// 16-byte vector (4 FP32 or 8 packed BF16) on the vector path, RC scalars on
+// the scalar path.  Keeping BF16 packed until use halves the registers that
+// loads in flight occupy.
+template <typename T, int VW, int RC>
+struct Landing {
+  using type = uint4;
+  __device__ __forceinline__ static void load(const void* base, int64_t row, int R, int sub,
+                                              int L, uint64_t pol, type& out) {
+    if (sub * VW < R)
+      out = ld_nc_hint_v4(reinterpret_cast<const uint4*>(static_cast<const T*>(base) + row * R) +
+                              sub,
+                          pol);
+    else
+      out = make_uint4(0u, 0u, 0u, 0u);
+  }
+  __device__ __forceinline__ static void unpack(const type& v, float* x) {
+    if constexpr (VW == 4) {
+      x[0] = __uint_as_float(v.x);
+      x[1] = __uint_as_float(v.y);
+      x[2] = __uint_as_float(v.z);
+      x[3] = __uint_as_float(v.w);
+    } else {
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        x[2 * j] = __uint_as_float(w[j] << 16);
+        x[2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+      }
+    }
+  }
+};
+
+template <typename T, int RC>
+struct Landing<T, 1, RC> {
+  struct type {
+    float v[RC];
+  };
+  __device__ __forceinline__ static void load(const void* base, int64_t row, int R, int sub,
+                                              int L, uint64_t, type& out) {
+#pragma unroll
+    for (int j = 0; j < RC; ++j) {
+      const int r = sub + L * j;
+      out.v[j] = r < R ? load_scalar<T>(base, row * R + r) : 0.f;
+    }
+  }
+  __device__ __forceinline__ static void unpack(const type& v, float* x) {
+#pragma unroll
+    for (int j = 0; j < RC; ++j) x[j] = v.v[j];
+  }
+};
+
+// NT: modes at compile time (0 = runtime); T: factor type; VW: values per lane
+// per 16-byte load (1 = scalar path); RC: rank chunks per lane (scalar path);
+// U: nonzeros in flight per lane group; MODE: output mode at compile time (3
+// modes only; -1 = runtime).
+template <int NT, typename T, int VW, int RC, int U, int MODE>
+__global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 : 2))
+    mttkrp_warp_kernel(const MttkrpArgs a, const int L) {
   constexpr int NV = VW * RC;
   const int N = NT > 0 ? NT : a.nmodes;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int G = 32 / L, sub = lane % L, gw = lane / L;
-  const int es = a.es, R = a.R, mode = a.mode;
+  const int es = a.es, R = a.R, mode = MODE >= 0 ? MODE : a.mode;
   const int TW = a.tile, K = TW / G;
   const int wb = blockIdx.x * kWarps + warp;
   if (wb >= a.nblk) return;
@@ -100,6 +156,16 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1) ? 3 : 2)) mttkrp
   // once per mode (evict first); factor rows are reused (evict last)
   const uint64_t pol_stream = make_policy((a.hints & 1) ? 1 : 0);
   const uint64_t pol_factor = make_policy((a.hints & 2) ? 2 : 0);
+  // static 3-mode vector path: this lane's 16-byte slice of the two input
+  // factors' rows (lanes past R read slice 0; their values are never stored)
+  const uint32_t rowb = (uint32_t)R * (uint32_t)sizeof(T);
+  const uint8_t* lane_base[2];
+  {
+    const int lsub = (sub * VW < R) ? sub : 0;
+    const int k1 = (MODE >= 0 ? MODE : 0) + 1, k2 = (MODE >= 0 ? MODE : 0) + 2;
+    lane_base[0] = static_cast<const uint8_t*>(a.factors[k1 % 3 < N ? k1 % 3 : 0]) + lsub * 16;
+    lane_base[1] = static_cast<const uint8_t*>(a.factors[k2 % 3 < N ? k2 % 3 : 0]) + lsub * 16;
+  }
 
   auto issue = [&](int t) {  // lane 0 only
     const int st = t % kStages;
@@ -248,48 +314,123 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1) ? 3 : 2)) mttkrp
       int cur = reinterpret_cast<const int*>(eb + (size_t)a0 * es)[mode];
       bool head = true;
       int prev_in_run = -1;
+      // input modes of this pass: km[j] = (mode + 1 + j) mod N, j < N - 1
+      constexpr int NI = (NT > 0 ? NT : 2) - 1;
       auto batch = [&](int e, int nb) {
+        // 1) element fields from shared memory, 2) every gather of the batch
+        // issued into packed registers, 3) products consumed in order
+        int rows[U];
+        float vals[U];
+        int ixs[U][NI];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (u < nb) {
+            const uint8_t* ep = eb + (size_t)(e + u) * es;
+            if constexpr (NT == 3 && MODE >= 0) {
+              const int4 v = *reinterpret_cast<const int4*>(ep);
+              const int f[3] = {v.x, v.y, v.z};
+              rows[u] = f[MODE];
+              ixs[u][0] = f[(MODE + 1) % 3];
+              ixs[u][1] = f[(MODE + 2) % 3];
+              vals[u] = __int_as_float(v.w);
+            } else {
+              const int* el = reinterpret_cast<const int*>(ep);
+              rows[u] = el[mode];
+              vals[u] = __int_as_float(el[N]);
+              int k = mode;
+#pragma unroll
+              for (int j = 0; j < NI; ++j) {
+                if (j < N - 1) {
+                  k = (k + 1 == N) ? 0 : k + 1;
+                  ixs[u][j] = el[k];
+                }
+              }
+            }
+          }
+        }
+        typename Landing<T, VW, RC>::type raw[U][NI];
+        if constexpr (NT == 3 && MODE >= 0 && VW > 1) {
+          // static modes: one 32 x 32 -> 64-bit multiply per row address
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+              if (u < nb)
+                raw[u][j] = ld_nc_hint_v4(lane_base[j] + (uint64_t)(uint32_t)ixs[u][j] * rowb,
+                                          pol_factor);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NI; ++j) {
+            if (j < N - 1) {
+              const int kj = (NT == 3 && MODE >= 0) ? (MODE + 1 + j) % 3 : (mode + 1 + j) % N;
+              const void* Ak = a.factors[kj];
+#pragma unroll
+              for (int u = 0; u < U; ++u)
+                if (u < nb)
+                  Landing<T, VW, RC>::load(Ak, ixs[u][j], R, sub, L, pol_factor, raw[u][j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (u < nb) {
+            float prod[NV], x[NV];
+            Landing<T, VW, RC>::unpack(raw[u][0], prod);
+#pragma unroll
+            for (int j = 1; j < NI; ++j) {
+              if (j < N - 1) {
+                Landing<T, VW, RC>::unpack(raw[u][j], x);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) prod[q] *= x[q];
+              }
+            }
+            if (rows[u] != cur) {
+              if (head) {
+                store_slot(2 * gw, cur, -2, acc);
+                head = false;
+              } else {
+                write_row_group(cur, acc, prev_in_run);
+              }
+              prev_in_run = cur;
+              cur = rows[u];
+#pragma unroll
+              for (int q = 0; q < NV; ++q) acc[q] = 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) acc[q] = fmaf(prod[q], vals[u], acc[q]);
+          }
+        }
+      };
+      // runtime number of modes: multiply each gathered slice in as it lands
+      auto batch_generic = [&](int e, int nb) {
         float prod[U][NV];
         float vals[U];
         int rows[U];
-        bool first_k = true;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (u < nb) {
             const int* el = reinterpret_cast<const int*>(eb + (size_t)(e + u) * es);
             rows[u] = el[mode];
             vals[u] = __int_as_float(el[N]);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) prod[u][q] = vals[u];
           }
         }
-#pragma unroll
-        for (int k = 0; k < (NT > 0 ? NT : kMaxModes); ++k) {
-          if (k >= N) break;
+        for (int k = 0; k < N; ++k) {
           if (k == mode) continue;
           const void* Ak = a.factors[k];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             if (u < nb) {
-              const int64_t ix = reinterpret_cast<const int*>(eb + (size_t)(e + u) * es)[k];
+              typename Landing<T, VW, RC>::type raw;
               float x[NV];
-              if constexpr (VW > 1) {
-                if (sub * VW < R) {
-                  Slice<T, VW>::load_hint(Ak, ix, R, sub, pol_factor, x);
-                } else {
+              Landing<T, VW, RC>::load(Ak, reinterpret_cast<const int*>(eb + (size_t)(e + u) * es)[k],
+                                       R, sub, L, pol_factor, raw);
+              Landing<T, VW, RC>::unpack(raw, x);
 #pragma unroll
-                  for (int j = 0; j < NV; ++j) x[j] = 0.f;
-                }
-              } else {
-#pragma unroll
-                for (int j = 0; j < NV; ++j) {
-                  const int r = rank_of(j);
-                  x[j] = (r < R) ? load_scalar<T>(Ak, ix * R + r) : 0.f;
-                }
-              }
-#pragma unroll
-              for (int j = 0; j < NV; ++j) prod[u][j] = first_k ? x[j] : prod[u][j] * x[j];
+              for (int q = 0; q < NV; ++q) prod[u][q] *= x[q];
             }
           }
-          first_k = false;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -304,16 +445,21 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1) ? 3 : 2)) mttkrp
               prev_in_run = cur;
               cur = rows[u];
 #pragma unroll
-              for (int j = 0; j < NV; ++j) acc[j] = 0.f;
+              for (int q = 0; q < NV; ++q) acc[q] = 0.f;
             }
 #pragma unroll
-            for (int j = 0; j < NV; ++j) acc[j] = fmaf(prod[u][j], vals[u], acc[j]);
+            for (int q = 0; q < NV; ++q) acc[q] += prod[u][q];
           }
         }
       };
       int e = a0;
-      for (; e + U <= b0; e += U) batch(e, U);
-      for (; e < b0; ++e) batch(e, 1);
+      if constexpr (NT > 0) {
+        for (; e + U <= b0; e += U) batch(e, U);
+        for (; e < b0; ++e) batch(e, 1);
+      } else {
+        for (; e + U <= b0; e += U) batch_generic(e, U);
+        for (; e < b0; ++e) batch_generic(e, 1);
+      }
       if (head) {
         store_slot(2 * gw, cur, -2, acc);
         if (sub == 0) srow[2 * gw + 1] = -1;
@@ -346,11 +492,11 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1) ? 3 : 2)) mttkrp
   if (crow >= 0) emit(crow, cprev, emitted == 0, true);
 }
 
-template <int NT, typename T, int VW, int RC, int U>
+template <int NT, typename T, int VW, int RC, int U, int MODE = -1>
 int launch_warp_kernel(const MttkrpArgs& a, int L, cudaStream_t s) {
   const int G = 32 / L;
   const size_t smem = (size_t)kWarps * warp_layout(a.es, a.tile, a.R, G).total;
-  auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U>;
+  auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U, MODE>;
   static size_t configured = 0;  // per instantiation: raise the dynamic smem limit once
   if (configured < smem) {
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,

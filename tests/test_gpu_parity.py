@@ -52,7 +52,8 @@ def run_all_modes(coo, vals, dims, R, dtype="f32", nblk=0, tile=0, seed=3, graph
 
 
 @pytest.mark.parametrize("N,R,dtype", [(3, 16, "f32"), (3, 32, "f32"), (3, 64, "f32"),
-                                       (3, 32, "bf16"), (4, 32, "f32"), (4, 64, "bf16"),
+                                       (3, 128, "f32"), (3, 16, "bf16"), (3, 32, "bf16"),
+                                       (3, 64, "bf16"), (4, 32, "f32"), (4, 64, "bf16"),
                                        (5, 16, "f32"), (6, 32, "f32"), (6, 32, "bf16")])
 def test_all_modes_match_oracle(N, R, dtype):
     dims = [60, 45, 30, 20, 12, 9][:N]
