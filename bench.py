@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the BF16 sweep, CP-loss and CP-ALS measurements")
     return ap.parse_args()
 
 
@@ -255,6 +257,66 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_events(fn, reps, stream):
+    """Mean ms of fn() over reps calls, CUDA events on `stream`, after one warm call."""
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, stream, world):
+    """BF16 factor sweep, CP-loss forward+backward throughput (FP32 and BF16) and one
+    graph-replayed CP-ALS iteration, on the same tensor."""
+    from paper_2405_08470_gb300 import Plan
+    from paper_2405_08470_gb300.cp import CPLoss
+    dev = F[0].device
+    nnz = int(vals_h.shape[0])
+    reps = max(2, min(args.steps, 5))
+    res = {}
+    # CP loss fwd+bwd on the FP32 plan (observed entries = the tensor's values)
+    Fg = [(f.float() * 0.1).requires_grad_(True) for f in F]
+
+    def loss_step(pl, fs):
+        for f in fs:
+            f.grad = None
+        CPLoss.apply(pl, *fs).backward()
+
+    ms32 = time_events(lambda: loss_step(plan, Fg), reps, stream)
+    res["cp_loss_fwd_bwd"] = {"f32": {"nnz_per_s": nnz / (ms32 * 1e-3), "ms": ms32}}
+    # BF16 factors: sweep time and CP loss on a BF16 plan of the same tensor
+    pb = Plan(coo_h, vals_h, spec.dims, R, dtype="bf16", nblk=args.nblk, tile=args.tile)
+    Fb = [f.to(torch.bfloat16) for f in F]
+    ob = [torch.empty_like(o) for o in outs]
+    msb = time_events(lambda: pb.sweep(Fb, ob, graph=True), reps, stream)
+    plan.sweep(F, outs, graph=True)
+    torch.cuda.synchronize()
+    num = sum(float(torch.linalg.vector_norm((a - b).double())) ** 2 for a, b in zip(ob, outs))
+    den = sum(float(torch.linalg.vector_norm(b.double())) ** 2 for b in outs)
+    res["bf16_sweep"] = {"ms_per_sweep": msb,
+                         "normwise_diff_vs_f32_sweep": (num / den) ** 0.5 if den else None}
+    Fbg = [(f * 0.1).to(torch.bfloat16).requires_grad_(True) for f in F]
+    msl = time_events(lambda: loss_step(pb, Fbg), reps, stream)
+    res["cp_loss_fwd_bwd"]["bf16"] = {"nnz_per_s": nnz / (msl * 1e-3), "ms": msl}
+    pb.close()
+    del ob, Fb, Fbg
+    # one CP-ALS iteration (FP64 Gram/Cholesky on the GPU), replayed as a CUDA graph
+    Fa = [f.clone() for f in F]
+    lam = torch.empty(R, device=dev)
+    fits = [plan.als_iter(Fa, lam)]  # eager run + capture
+    t0 = time.perf_counter()
+    for _ in range(3):
+        fits.append(plan.als_iter(Fa, lam))
+    t_als = (time.perf_counter() - t0) / 3 * 1e3
+    res["cp_als"] = {"ms_per_iter_host_timed_incl_fit_sync": t_als, "fits": fits}
+    return res
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
@@ -354,6 +416,10 @@ def main():
         e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    extra = {}
+    if not args.no_extras:
+        extra = extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, stream, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         S, dt = cpu_oracle_sample(coo_h, vals_h, spec.dims, R, args.cpu_seconds, fseed)
@@ -391,6 +457,7 @@ def main():
             "plan_seconds": plan_s,
             "touched_rows": touched,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

@@ -59,7 +59,7 @@ typedef struct {
   int partition;    /* 0 = contiguous split with heavy-row splitting (only one)  */
   int nblk;         /* blocks per mode (warp blocks for variant 0, CTA blocks for
                        variant 1); 0 = size-based default                         */
-  int tile;         /* nonzeros per staged warp tile: 0 (= 128 for 3 modes, less
+  int tile;         /* nonzeros per staged warp tile: 0 (= 256 for 3 modes, less
                        for wider elements), 32, 64, 128 or 256                    */
   size_t max_bytes; /* cap on the plan's device memory; 0 = no cap               */
   int checks;       /* 1 = synchronize and read the device error word after every

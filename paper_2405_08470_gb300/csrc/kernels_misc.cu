@@ -20,7 +20,8 @@ size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype) {
   size_t m = 0;
   for (bool al : {true, false}) {
     const LaneCfg c = lane_config(R, dtype, al);
-    m = std::max(m, (size_t)kWarps * warp_layout(es, tile, R, 32 / c.L).total);
+    const int G = 32 / c.L;
+    m = std::max(m, (size_t)kWarps * warp_layout(es, warp_tile_for(tile, G), R, G).total);
   }
   return m;
 }
@@ -31,38 +32,49 @@ int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s) {
   return a.dtype == SPM_DTYPE_BF16 ? launch_mttkrp_bf16(a, c, s) : launch_mttkrp_f32(a, c, s);
 }
 
-// One warp per split row: sum the block partials in ascending block order,
-// zero the empty rows before it (and after it, for the last nonempty row),
-// write the row once.
+// One CTA per split row: warp w sums the partials of blocks first_blk + w,
+// first_blk + w + 8, ... (lanes over R), the 8 warp sums are added in warp
+// order (a fixed order: results are bit-identical run to run); the empty rows
+// before the row (and after it, for the last nonempty row) are zeroed; the row
+// is written once.
 __global__ void __launch_bounds__(256) splitrow_fixup_kernel(const float* __restrict__ part,
                                                              const SplitRow* __restrict__ splits,
                                                              int nsplit, float* __restrict__ out,
                                                              int64_t out_rows, int R,
                                                              const float* scale) {
-  const int w = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w >= nsplit) return;
-  const SplitRow sr = splits[w];
+  __shared__ float red[8][kMaxRank];
+  if ((int)blockIdx.x >= nsplit) return;
+  const SplitRow sr = splits[blockIdx.x];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float sc = scale ? __ldg(scale) : 1.0f;
-  for (int64_t z = (int64_t)sr.prev_row + 1; z < sr.row; ++z)
-    for (int r = lane; r < R; r += 32) out[z * R + r] = 0.f;
+  const int nb = sr.last_blk - sr.first_blk + 1;
   for (int r = lane; r < R; r += 32) {
     float acc = 0.f;
-    for (int b = sr.first_blk; b <= sr.last_blk; ++b) {
-      const int slot = (b == sr.first_blk) ? sr.first_slot : 0;
-      acc += part[((size_t)b * 2 + slot) * R + r];
+    for (int i = w; i < nb; i += 8) {
+      const int b = sr.first_blk + i;
+      acc += __ldg(part + ((size_t)b * 2 + (i == 0 ? sr.first_slot : 0)) * R + r);
     }
+    red[w][r] = acc;
+  }
+  const int64_t gap0 = (int64_t)sr.prev_row + 1, ngap = ((int64_t)sr.row - gap0) * R;
+  for (int64_t i = threadIdx.x; i < ngap; i += blockDim.x) out[gap0 * R + i] = 0.f;
+  if (sr.is_last) {
+    const int64_t t0 = (int64_t)sr.row + 1, nt = (out_rows - t0) * R;
+    for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) out[t0 * R + i] = 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc += red[q][r];
     out[(int64_t)sr.row * R + r] = acc * sc;
   }
-  if (sr.is_last)
-    for (int64_t z = (int64_t)sr.row + 1; z < out_rows; ++z)
-      for (int r = lane; r < R; r += 32) out[z * R + r] = 0.f;
 }
 
 int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* out,
                  int64_t out_rows, int R, const float* scale, cudaStream_t s) {
   if (nsplit <= 0) return SPM_OK;
-  splitrow_fixup_kernel<<<(nsplit + 7) / 8, 256, 0, s>>>(part, splits, nsplit, out, out_rows, R,
-                                                         scale);
+  splitrow_fixup_kernel<<<nsplit, 256, 0, s>>>(part, splits, nsplit, out, out_rows, R, scale);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SPM_OK : cuda_fail(e, "splitrow_fixup_kernel launch");
 }

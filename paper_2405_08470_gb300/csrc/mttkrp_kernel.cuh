@@ -32,7 +32,7 @@
 
 namespace spm {
 
-constexpr int kStages = 3;  // tiles per warp ring (two in flight while one is used)
+constexpr int kStages = 2;  // tiles per warp ring (one in flight while one is used)
 constexpr int kWarps = kThreads / 32;
 
 // Per-warp shared-memory layout (bytes, in order).
@@ -40,13 +40,18 @@ struct WarpLayout {
   size_t ebuf, npbuf, sacc, cacc, srow, sprev, mbar, total;
 };
 
+// Remap ids staged per tile: tw + 3 ids at most (the copy starts at the
+// 16-byte boundary at or below the tile) rounded up to a multiple of 4 ints,
+// so that every stage's bulk-copy destination stays 16-byte aligned.
+__host__ __device__ inline int np_stage_ints(int tw) { return (tw + 8 + 3) & ~3; }
+
 __host__ __device__ inline WarpLayout warp_layout(int es, int tw, int R, int G) {
   WarpLayout l;
   size_t o = 0;
   l.ebuf = o;
   o += (size_t)kStages * tw * es;
   l.npbuf = o;
-  o += (size_t)kStages * (tw + 8) * 4;
+  o += (size_t)kStages * np_stage_ints(tw) * 4;
   l.sacc = o;
   o += (size_t)2 * G * R * 4;
   l.cacc = o;
@@ -62,8 +67,6 @@ __host__ __device__ inline WarpLayout warp_layout(int es, int tw, int R, int G) 
   return l;
 }
 
-// Default nonzeros per warp tile: small enough that three CTAs of 8 warps fit an SM.
-__host__ __device__ inline int warp_tile(int es) { return es <= 16 ? 128 : (es <= 32 ? 64 : 32); }
 
 // Registers a gathered factor-row slice lands in before it is used: one
 // 16-byte vector (4 FP32 or 8 packed BF16) on the vector path, RC scalars on
@@ -183,7 +186,8 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
     bulk_g2s_hint(ebuf + (size_t)st * TW * es, a.elems_in + (size_t)tlo * es, ebytes, &mbar[st],
                   pol_stream);
     if (remap)
-      bulk_g2s_hint(npbuf + st * (TW + 8), a.next_pos + np0, npbytes, &mbar[st], pol_stream);
+      bulk_g2s_hint(npbuf + st * np_stage_ints(TW), a.next_pos + np0, npbytes, &mbar[st],
+                    pol_stream);
   };
 
   if (lane == 0) {
@@ -191,10 +195,8 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
     fence_mbar_init();
   }
   __syncwarp();
-  if (lane == 0) {
-    issue(0);
-    if (ntiles > 1) issue(1);
-  }
+  if (lane == 0)
+    for (int q = 0; q < kStages - 1 && q < ntiles; ++q) issue(q);
 
   auto rank_of = [&](int j) -> int {
     if constexpr (VW > 1) return sub * VW + j;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
         for (int r = lane; r < R; r += 32) out[z * R + r] = 0.f;
   };
 
-  int issued = min(ntiles, 2);
+  int issued = min(ntiles, kStages - 1);
   for (int t = 0; t < ntiles; ++t) {
     const int st = t % kStages;
     const bool ok = mbar_wait_bounded(&mbar[st], (uint32_t)((t / kStages) & 1));
@@ -281,17 +283,17 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
       }
       return;
     }
-    // the stage of tile t+2 held tile t-1, whose readers passed the last __syncwarp
-    if (lane == 0 && t + 2 < ntiles) {
-      issue(t + 2);
-      issued = t + 3;
+    // the stage of tile t+kStages-1 held tile t-1, whose readers passed the last __syncwarp
+    if (lane == 0 && t + kStages - 1 < ntiles) {
+      issue(t + kStages - 1);
+      issued = t + kStages;
     }
     const int tlo = lo + t * TW;
     const int n = min(TW, hi - tlo);
     const uint8_t* eb = ebuf + (size_t)st * TW * es;
 
     if (remap) {  // Algorithm 3: every element to its place in the next mode's order
-      const int32_t* np = npbuf + st * (TW + 8) + (tlo & 3);
+      const int32_t* np = npbuf + st * np_stage_ints(TW) + (tlo & 3);
       const int nv = es / 16;
       for (int i = lane; i < n * nv; i += 32) {
         const int e = i / nv, c = i - e * nv;
@@ -492,9 +494,20 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
   if (crow >= 0) emit(crow, cprev, emitted == 0, true);
 }
 
+// Nonzeros per warp tile for a requested size: G runs of an odd length K, so
+// that the groups' elements fall on distinct shared-memory banks.
+__host__ __device__ inline int warp_tile_for(int tile, int G) {
+  int K = tile / G;
+  if (K < 1) K = 1;
+  if (!(K & 1)) K += 1;
+  return G * K;
+}
+
 template <int NT, typename T, int VW, int RC, int U, int MODE = -1>
-int launch_warp_kernel(const MttkrpArgs& a, int L, cudaStream_t s) {
+int launch_warp_kernel(const MttkrpArgs& a0, int L, cudaStream_t s) {
   const int G = 32 / L;
+  MttkrpArgs a = a0;
+  a.tile = warp_tile_for(a0.tile, G);
   const size_t smem = (size_t)kWarps * warp_layout(a.es, a.tile, a.R, G).total;
   auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U, MODE>;
   static size_t configured = 0;  // per instantiation: raise the dynamic smem limit once

@@ -112,7 +112,8 @@ int default_nblk(int64_t nnz, int num_sms, int variant) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(nb, 1 << 22));
 }
 
-int default_tile(int es) { return es <= 16 ? 128 : (es <= 32 ? 64 : 32); }
+// default nonzeros per warp tile (before rounding each group's run to an odd length)
+int default_tile(int es) { return es <= 16 ? 128 : (es <= 32 ? 128 : 64); }
 
 // Position -> index of the nonempty row holding it (ustart ascending, size nu+1).
 static inline int64_t row_index_of(const std::vector<int64_t>& ustart, int64_t pos) {
