@@ -70,6 +70,7 @@ typedef struct {
                        shared memory by bulk async copies (default); 1 = one CTA
                        per block, each lane group streams one contiguous run     */
   int unroll;       /* nonzeros in flight per lane group in form 0: 0 (= 8), 4, 8 */
+  int stages;       /* tiles per warp ring in form 0: 0 (= 3), 2, 3 or 4        */
   int cache_hints;  /* form 0 L2 policy: -1 = none, 0 = default (= 3); bit0: the
                        nonzero stream, remap ids and remapped copy evict first;
                        bit1: factor rows evict last                               */

@@ -146,6 +146,7 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   a.variant = p->variant;
   a.hints = p->hints;
   a.unroll = p->unroll;
+  a.stages = p->stages;
   int st = launch_mttkrp(a, p->stream);
   if (st) return st;
   return launch_fixup(p->d_part, d.splits, d.nsplit, out, a.out_rows, p->R, scale, p->stream);
@@ -220,6 +221,8 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   if (o.variant < 0 || o.variant > 1) return fail(SPM_ERR_INVALID_ARG, "variant must be 0 or 1");
   if (o.unroll != 0 && o.unroll != 4 && o.unroll != 8)
     return fail(SPM_ERR_INVALID_ARG, "unroll must be 0, 4 or 8");
+  if (o.stages != 0 && (o.stages < 2 || o.stages > 4))
+    return fail(SPM_ERR_INVALID_ARG, "stages must be 0 or in [2, 4]");
   if (o.cache_hints < -1 || o.cache_hints > 3)
     return fail(SPM_ERR_INVALID_ARG, "cache_hints must be in [-1, 3]");
 
@@ -231,6 +234,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->dtype = o.factor_dtype;
   p->variant = o.variant;
   p->unroll = o.unroll ? o.unroll : 8;
+  p->stages = o.stages ? o.stages : 3;
   p->hints = o.cache_hints == 0 ? 3 : (o.cache_hints < 0 ? 0 : o.cache_hints);
   p->checks = o.checks;
   p->host_only = o.host_only;
@@ -240,7 +244,8 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->es = ((4 * nmodes + 4) + 15) & ~15;
   p->tile = o.tile ? o.tile : default_tile(p->es);
   // keep the staged tiles within shared memory for wide elements
-  while (p->tile > 32 && mttkrp_smem_bytes(p->es, p->tile, p->R, p->dtype) > 200 * 1024)
+  while (p->tile > 32 &&
+         mttkrp_smem_bytes(p->es, p->tile, p->R, p->dtype, p->stages) > 200 * 1024)
     p->tile /= 2;
   if (!p->host_only) {
     cudaError_t e = cudaGetDevice(&p->device);

@@ -285,7 +285,8 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   for (int n : {24, 48, 96, 192}) {
     if ((int64_t)n * p->num_sms * 128 > p->nnz && n > 24) continue;
     for (int t : {128, 256})
-      if (mttkrp_smem_bytes(p->es, t, p->R, p->dtype) <= 200 * 1024) cands.push_back({n, t, 0});
+      if (mttkrp_smem_bytes(p->es, t, p->R, p->dtype, p->stages) <= 200 * 1024)
+        cands.push_back({n, t, 0});
   }
   for (int n : {4, 8, 16, 32}) {
     if ((int64_t)n * p->num_sms * 1024 > p->nnz && n > 4) continue;

@@ -62,6 +62,7 @@ struct spmttkrp_plan {
   int variant = 0;  // fused-kernel form (see MttkrpArgs::variant)
   int hints = 3;    // L2 cache policy bits of the fused kernel (see MttkrpArgs)
   int unroll = 0;   // nonzeros in flight per lane group of the warp-block form
+  int stages = 3;   // tiles per warp ring of the warp-block form
   int64_t nnz = 0;
   int es = 16;  // element stride in bytes: {int32 idx[N]; float val}, rounded up to 16
   std::vector<int64_t> dims;
@@ -140,6 +141,7 @@ struct MttkrpArgs {
   int variant;             // 0 = warp blocks, staged tiles; 1 = CTA blocks, direct runs
   int hints;               // bit0: streams evict_first in L2; bit1: factor rows evict_last
   int unroll;              // nonzeros in flight per lane group (4 or 8; 0 = default)
+  int stages;              // tiles per warp ring of the staged form (2..4)
 };
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
 int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* out,
@@ -147,6 +149,6 @@ int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* o
 int launch_zero_rows(float* out, int64_t rows, int R, cudaStream_t s);
 int launch_remap_only(const uint8_t* in, uint8_t* out, const int32_t* next_pos, int64_t nnz,
                       int es, cudaStream_t s);
-size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype);
+size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype, int stages);
 
 }  // namespace spm

@@ -16,12 +16,12 @@ static LaneCfg cfg_for(const MttkrpArgs& a) {
   return lane_config(a.R, a.dtype, al);
 }
 
-size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype) {
+size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype, int stages) {
   size_t m = 0;
   for (bool al : {true, false}) {
     const LaneCfg c = lane_config(R, dtype, al);
     const int G = 32 / c.L;
-    m = std::max(m, (size_t)kWarps * warp_layout(es, warp_tile_for(tile, G), R, G).total);
+    m = std::max(m, (size_t)kWarps * warp_layout(es, warp_tile_for(tile, G), R, G, stages).total);
   }
   return m;
 }

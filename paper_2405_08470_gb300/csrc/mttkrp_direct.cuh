@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kThreads, 3) mttkrp_direct_kernel(const Mttkrp
   const int es = a.es, R = a.R, mode = a.mode;
   const int sub = lane % L, gw = lane / L, gi = warp * G + gw;
 
-  extern __shared__ __align__(16) uint8_t smem[];
+  extern __shared__ __align__(128) uint8_t smem[];
   float* sacc = reinterpret_cast<float*>(smem);
   int* srow = reinterpret_cast<int*>(smem + (size_t)2 * NG * R * 4);
   int* sprev = srow + 2 * NG;
