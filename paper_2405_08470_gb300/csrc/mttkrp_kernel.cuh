@@ -325,6 +325,32 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
         }
       }
     }
+    // rows are sorted within a run: if the batch's last nonzero is still in the
+    // current row, every nonzero of the batch is, and no per-nonzero check is needed
+    bool same_row = true;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (u == nb - 1) same_row = (rows[u] == cur);
+    if (same_row) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (u < nb) {
+          float prod[NV], x[NV];
+          Landing<T, VW, RC>::unpack(raw[u][0], prod);
+#pragma unroll
+          for (int j = 1; j < NI; ++j) {
+            if (j < N - 1) {
+              Landing<T, VW, RC>::unpack(raw[u][j], x);
+#pragma unroll
+              for (int q = 0; q < NV; ++q) prod[q] *= x[q];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < NV; ++q) acc[q] = fmaf(prod[q], vals[u], acc[q]);
+        }
+      }
+      return;
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (u < nb) {
