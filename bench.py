@@ -52,6 +52,7 @@ def parse():
                     help="0 warp blocks with staged tiles, 1 CTA blocks with direct runs")
     ap.add_argument("--unroll", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--element-bytes", type=int, default=0)
     ap.add_argument("--hints", type=int, default=0, help="-1 none, 0 default, 1..3 bits")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -343,7 +344,7 @@ def main():
     t0 = time.perf_counter()
     plan = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, nblk=args.nblk, tile=args.tile,
                 variant=args.variant, unroll=args.unroll, cache_hints=args.hints,
-                stages=args.stages)
+                stages=args.stages, element_bytes=args.element_bytes)
     plan_s = time.perf_counter() - t0
     info = plan.info()
     outs = [torch.empty(d, R, device=dev) for d in spec.dims]
@@ -442,6 +443,7 @@ def main():
                                        "CTA blocks, direct runs"][args.variant],
                        "unroll": args.unroll or 8, "cache_hints": args.hints,
                        "stages": args.stages or 3,
+                       "element_bytes": info["elem_bytes"],
                        "l2": "inputs larger than L2 (element stream "
                              f"{nnz * info['elem_bytes'] / 1e9:.2f} GB per mode)",
                        "parallelism": f"replicas x{world}"},

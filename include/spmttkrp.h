@@ -71,6 +71,10 @@ typedef struct {
                        per block, each lane group streams one contiguous run     */
   int unroll;       /* nonzeros in flight per lane group in form 0: 0 (= 8), 4, 8 */
   int stages;       /* tiles per warp ring in form 0: 0 (= 3), 2, 3 or 4        */
+  int element_bytes;/* stride of a stored nonzero: 0 = smallest multiple of 16
+                       bytes (16 for 3 modes, 32 for 4..7), or 32 (3 modes padded
+                       to a whole 32-byte sector, so remap stores write whole
+                       sectors)                                                   */
   int cache_hints;  /* form 0 L2 policy: -1 = none, 0 = default (= 3); bit0: the
                        nonzero stream, remap ids and remapped copy evict first;
                        bit1: factor rows evict last                               */

@@ -43,6 +43,7 @@ class Opts(ctypes.Structure):
                 ("max_bytes", ctypes.c_size_t), ("checks", ctypes.c_int),
                 ("host_only", ctypes.c_int), ("variant", ctypes.c_int),
                 ("unroll", ctypes.c_int), ("stages", ctypes.c_int),
+                ("element_bytes", ctypes.c_int),
                 ("cache_hints", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
@@ -118,7 +119,7 @@ class Plan:
     def __init__(self, coo, vals, dims: Sequence[int], rank: int, dtype: str = "f32",
                  nblk: int = 0, tile: int = 0, max_bytes: int = 0, checks: bool = False,
                  host_only: bool = False, stream=None, variant: int = 0, unroll: int = 0,
-                 cache_hints: int = 0, stages: int = 0):
+                 cache_hints: int = 0, stages: int = 0, element_bytes: int = 0):
         L = lib()
         coo = np.ascontiguousarray(np.asarray(coo.cpu() if hasattr(coo, "cpu") else coo,
                                               dtype=np.int64))
@@ -136,6 +137,7 @@ class Plan:
         o.checks, o.host_only = int(bool(checks)), int(bool(host_only))
         o.variant = int(variant)
         o.unroll, o.cache_hints, o.stages = int(unroll), int(cache_hints), int(stages)
+        o.element_bytes = int(element_bytes)
         o.stream = None if host_only else _stream_ptr(stream)
         d = np.asarray(self.dims, dtype=np.int64)
         h = ctypes.c_void_p()

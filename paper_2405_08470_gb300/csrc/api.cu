@@ -242,6 +242,13 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->stream = (cudaStream_t)o.stream;
   p->dims.assign(dims, dims + nmodes);
   p->es = ((4 * nmodes + 4) + 15) & ~15;
+  if (o.element_bytes != 0) {
+    if (o.element_bytes != 32 || p->es > 32) {
+      delete p;
+      return fail(SPM_ERR_INVALID_ARG, "element_bytes must be 0, or 32 for up to 7 modes");
+    }
+    p->es = 32;
+  }
   p->tile = o.tile ? o.tile : default_tile(p->es);
   // keep the staged tiles within shared memory for wide elements
   while (p->tile > 32 &&

@@ -7,7 +7,9 @@ namespace spm {
 static int launch_direct_float(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
   if (c.vec) {
     switch (a.nmodes) {
-      case 3: return launch_direct<3, float, 4, 1, 4>(a, c.L, s);
+      case 3:
+        if (a.es == 16) return launch_direct<3, float, 4, 1, 4>(a, c.L, s);
+        return launch_direct<0, float, 4, 1, 2>(a, c.L, s);
       case 4: return launch_direct<4, float, 4, 1, 4>(a, c.L, s);
       case 5: return launch_direct<5, float, 4, 1, 4>(a, c.L, s);
       case 6: return launch_direct<6, float, 4, 1, 4>(a, c.L, s);
@@ -27,6 +29,13 @@ int launch_mttkrp_f32(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
   if (c.vec) {
     switch (a.nmodes) {
       case 3:
+        if (a.es == 32) {  // elements padded to a full 32-byte sector
+          switch (a.mode) {
+            case 0: return launch_warp_kernel<3, float, 4, 1, 8, 0, 32>(a, c.L, s);
+            case 1: return launch_warp_kernel<3, float, 4, 1, 8, 1, 32>(a, c.L, s);
+            default: return launch_warp_kernel<3, float, 4, 1, 8, 2, 32>(a, c.L, s);
+          }
+        }
         if (a.unroll == 4) {
           switch (a.mode) {
             case 0: return launch_warp_kernel<3, float, 4, 1, 4, 0>(a, c.L, s);

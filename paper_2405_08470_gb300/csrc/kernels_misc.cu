@@ -99,9 +99,22 @@ int launch_zero_rows(float* out, int64_t rows, int R, cudaStream_t s) {
 }
 
 // Remap without compute (Algorithm 3 alone): T_out[next_pos[p]] = T_in[p].
+// Elements whose stride is a multiple of 32 bytes move in whole 32-byte
+// sectors (one 256-bit store each), others in 16-byte pieces.
 __global__ void remap_only_kernel(const uint4* __restrict__ in, uint4* __restrict__ out,
                                   const int32_t* __restrict__ next_pos, int64_t nnz, int nv) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if ((nv & 1) == 0) {
+    const int nw = nv / 2;
+    const uint64_t pol = make_policy(1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz * nw; i += stride) {
+      const int64_t p = i / nw;
+      const int c = (int)(i - p * nw);
+      const uint4 lo = __ldg(in + p * nv + 2 * c), hi = __ldg(in + p * nv + 2 * c + 1);
+      st_hint_v8(out + (int64_t)__ldg(next_pos + p) * nv + 2 * c, lo, hi, pol);
+    }
+    return;
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz * nv; i += stride) {
     const int64_t p = i / nv;
     const int c = (int)(i - p * nv);

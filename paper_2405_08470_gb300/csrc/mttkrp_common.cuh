@@ -114,6 +114,18 @@ __device__ __forceinline__ void st_hint_v4(void* ptr, uint4 v, uint64_t policy) 
                : "memory");
 }
 
+// 32-byte global store (a whole DRAM sector) with an L2 cache policy; the
+// address must be 32-byte aligned.  A full-sector write needs no read of the
+// sector's old contents, unlike a 16-byte write into it.
+__device__ __forceinline__ void st_hint_v8(void* ptr, uint4 lo, uint4 hi, uint64_t policy) {
+  asm volatile(
+      "st.global.L1::no_allocate.L2::cache_hint.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8}, "
+      "%9;" ::"l"(ptr),
+      "r"(lo.x), "r"(lo.y), "r"(lo.z), "r"(lo.w), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w),
+      "l"(policy)
+      : "memory");
+}
+
 // 16-byte read-only global load with an L2 cache policy.
 __device__ __forceinline__ uint4 ld_nc_hint_v4(const void* ptr, uint64_t policy) {
   uint4 v;

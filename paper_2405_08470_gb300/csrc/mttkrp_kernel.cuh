@@ -122,8 +122,9 @@ struct Landing<T, 1, RC> {
 // NT: modes at compile time (0 = runtime); T: factor type; VW: values per lane
 // per 16-byte load (1 = scalar path); RC: rank chunks per lane (scalar path);
 // U: nonzeros in flight per lane group; MODE: output mode at compile time (3
-// modes only; -1 = runtime).
-template <int NT, typename T, int VW, int RC, int U, int MODE>
+// modes only; -1 = runtime); ESB: element bytes when fixed (0 = the smallest
+// multiple of 16 that holds N indices and the value).
+template <int NT, typename T, int VW, int RC, int U, int MODE, int ESB = 0>
 __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 : 2))
     mttkrp_warp_kernel(const MttkrpArgs a, const int L) {
   constexpr int NV = VW * RC;
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int G = 32 / L, sub = lane % L, gw = lane / L;
   // element stride: a compile-time constant when the number of modes is
-  constexpr int ES_C = NT > 0 ? (((4 * NT + 4) + 15) & ~15) : 0;
+  constexpr int ES_C = ESB > 0 ? ESB : (NT > 0 ? (((4 * NT + 4) + 15) & ~15) : 0);
   const int es = NT > 0 ? ES_C : a.es;
   const int R = a.R, mode = MODE >= 0 ? MODE : a.mode;
   const int TW = a.tile, K = TW / G, NPK = np_stage_ints(K);
@@ -460,11 +461,21 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
 
     if (remap) {  // Algorithm 3: every element to its place in the next mode's order
       const int32_t* np = npbuf + (st * G + gw) * NPK + (seg & 3);
-      const int nv = es / 16;  // 16-byte vectors per element (constant when NT > 0)
-      for (int i = sub; i < n * nv; i += L) {
-        const int e = (nv == 1) ? i : i / nv, c = (nv == 1) ? 0 : i - e * nv;
-        const uint4 v = reinterpret_cast<const uint4*>(eb + (size_t)e * es)[c];
-        st_hint_v4(reinterpret_cast<uint4*>(a.elems_out + (size_t)np[e] * es) + c, v, pol_stream);
+      if (es % 32 == 0) {  // whole 32-byte sectors per store (no read of the old sector)
+        const int nv = es / 32;
+        for (int i = sub; i < n * nv; i += L) {
+          const int e = (nv == 1) ? i : i / nv, c = (nv == 1) ? 0 : i - e * nv;
+          const uint4* src = reinterpret_cast<const uint4*>(eb + (size_t)e * es) + 2 * c;
+          st_hint_v8(a.elems_out + (size_t)np[e] * es + 32 * c, src[0], src[1], pol_stream);
+        }
+      } else {
+        const int nv = es / 16;  // 16-byte vectors per element (constant when NT > 0)
+        for (int i = sub; i < n * nv; i += L) {
+          const int e = (nv == 1) ? i : i / nv, c = (nv == 1) ? 0 : i - e * nv;
+          const uint4 v = reinterpret_cast<const uint4*>(eb + (size_t)e * es)[c];
+          st_hint_v4(reinterpret_cast<uint4*>(a.elems_out + (size_t)np[e] * es) + c, v,
+                     pol_stream);
+        }
       }
     }
 
@@ -540,13 +551,13 @@ __host__ __device__ inline int warp_tile_for(int tile, int G) {
   return G * K;
 }
 
-template <int NT, typename T, int VW, int RC, int U, int MODE = -1>
+template <int NT, typename T, int VW, int RC, int U, int MODE = -1, int ESB = 0>
 int launch_warp_kernel(const MttkrpArgs& a0, int L, cudaStream_t s) {
   const int G = 32 / L;
   MttkrpArgs a = a0;
   a.tile = warp_tile_for(a0.tile, G);
   const size_t smem = (size_t)kWarps * warp_layout(a.es, a.tile, a.R, G, a.stages).total;
-  auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U, MODE>;
+  auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U, MODE, ESB>;
   static size_t configured = 0;  // per instantiation: raise the dynamic smem limit once
   if (configured < smem) {
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,

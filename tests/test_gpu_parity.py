@@ -29,12 +29,13 @@ def built():
 
 
 def run_all_modes(coo, vals, dims, R, dtype="f32", nblk=0, tile=0, seed=3, graph=False,
-                  check_order=True, scale=1.0, variant=0):
+                  check_order=True, scale=1.0, variant=0, element_bytes=0):
     c, v = coo.numpy(), vals.numpy()
     F = synth.make_factors(dims, R, seed=seed, scale=scale)
     tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
     Fd = [f.to(tdt).cuda() for f in F]
-    p = Plan(c, v, dims, R, dtype=dtype, nblk=nblk, tile=tile, checks=True, variant=variant)
+    p = Plan(c, v, dims, R, dtype=dtype, nblk=nblk, tile=tile, checks=True, variant=variant,
+             element_bytes=element_bytes)
     N = len(dims)
     outs = [torch.full((d, R), float("nan"), device="cuda") for d in dims]
     for n in range(N):
@@ -198,4 +199,23 @@ def test_determinism_graph_and_remap():
     torch.cuda.synchronize()
     assert torch.equal(out, o1[1])
     p.device_status()
+    p.close()
+
+
+@pytest.mark.parametrize("variant,dtype,R", [(0, "f32", 32), (0, "bf16", 32), (1, "f32", 32),
+                                             (0, "f32", 17)])
+def test_padded_32_byte_elements(variant, dtype, R):
+    # 3-mode nonzeros stored in whole 32-byte sectors: same results, same remap order
+    dims = (300, 200, 100)
+    coo, vals = synth.make_coo(dims, 9000, (1.1, 1.1, 0.0), seed=R + variant)
+    p, got, F, Fh = run_all_modes(coo, vals, dims, R, dtype=dtype, nblk=29, variant=variant,
+                                  element_bytes=32)
+    assert p.info()["elem_bytes"] == 32
+    c, v = coo.numpy(), vals.numpy()
+    for n in range(3):
+        assert O.relerr(got[n], O.mttkrp(c, v, dims, Fh, n)) <= F32_TOL
+    for m in (2, 0):  # remap-only passes move whole sectors too
+        p.remap(m)
+        idx, _ = p.elements()
+        assert np.array_equal(idx, O.elements_in_order(c, v, m)[0])
     p.close()
