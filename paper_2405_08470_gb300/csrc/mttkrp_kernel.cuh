@@ -338,16 +338,33 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
         if (u < nb) {
           float prod[NV], x[NV];
           Landing<T, VW, RC>::unpack(raw[u][0], prod);
+          if constexpr (NV % 2 == 0) {  // paired FP32: half the instructions
+            float2* p2 = reinterpret_cast<float2*>(prod);
 #pragma unroll
-          for (int j = 1; j < NI; ++j) {
-            if (j < N - 1) {
-              Landing<T, VW, RC>::unpack(raw[u][j], x);
+            for (int j = 1; j < NI; ++j) {
+              if (j < N - 1) {
+                Landing<T, VW, RC>::unpack(raw[u][j], x);
+                const float2* x2 = reinterpret_cast<const float2*>(x);
 #pragma unroll
-              for (int q = 0; q < NV; ++q) prod[q] *= x[q];
+                for (int q = 0; q < NV / 2; ++q) p2[q] = mul2(p2[q], x2[q]);
+              }
             }
-          }
+            float2* a2 = reinterpret_cast<float2*>(acc);
+            const float2 vv = make_float2(vals[u], vals[u]);
 #pragma unroll
-          for (int q = 0; q < NV; ++q) acc[q] = fmaf(prod[q], vals[u], acc[q]);
+            for (int q = 0; q < NV / 2; ++q) a2[q] = fma2(p2[q], vv, a2[q]);
+          } else {
+#pragma unroll
+            for (int j = 1; j < NI; ++j) {
+              if (j < N - 1) {
+                Landing<T, VW, RC>::unpack(raw[u][j], x);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) prod[q] *= x[q];
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) acc[q] = fmaf(prod[q], vals[u], acc[q]);
+          }
         }
       }
       return;
@@ -462,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
     if (remap) {  // Algorithm 3: every element to its place in the next mode's order
       const int32_t* np = npbuf + (st * G + gw) * NPK + (seg & 3);
       if (es % 32 == 0) {  // whole 32-byte sectors per store (no read of the old sector)
-        const int nv = es / 32;
+        const int nv = es >= 32 ? es / 32 : 1;
         for (int i = sub; i < n * nv; i += L) {
           const int e = (nv == 1) ? i : i / nv, c = (nv == 1) ? 0 : i - e * nv;
           const uint4* src = reinterpret_cast<const uint4*>(eb + (size_t)e * es) + 2 * c;
