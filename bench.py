@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--element-bytes", type=int, default=0)
     ap.add_argument("--hints", type=int, default=0, help="-1 none, 0 default, 1..3 bits")
+    ap.add_argument("--keep-base", action="store_true",
+                    help="keep the mode-0 copy resident: the last mode's pass writes no remap")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -106,13 +108,14 @@ def workload_tensors(name, nnz_override, device):
     return spec, coo, vals
 
 
-def compulsory_bytes(dims, nnz, R, s, touched, N):
+def compulsory_bytes(dims, nnz, R, s, touched, N, keep_base=False):
     """Algorithmic bytes of mode n's fused pass (elements read + next_pos + remapped write,
-    each touched factor row once, output written once)."""
+    each touched factor row once, output written once).  With the mode-0 copy kept
+    resident the last mode's pass reads no next_pos and writes no remapped copy."""
     E = 4 * N + 4
     out = []
     for n in range(N):
-        b = nnz * (E + 4 + E)
+        b = nnz * (E + 4 + E) if not (keep_base and n == N - 1) else nnz * E
         b += sum(touched[k] * R * s for k in range(N) if k != n)
         b += dims[n] * R * 4
         out.append(b)
@@ -307,6 +310,23 @@ def extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, strea
     res["cp_loss_fwd_bwd"]["bf16"] = {"nnz_per_s": nnz / (msl * 1e-3), "ms": msl}
     pb.close()
     del ob, Fb, Fbg
+    # the same FP32 sweep with the mode-0 copy kept resident (N-1 remap scatters per
+    # sweep), and with 3-mode nonzeros padded to whole 32-byte sectors
+    variants = {"keep_base_sweep": dict(keep_base=True)}
+    if len(spec.dims) == 3:
+        variants["element_bytes_32_sweep"] = dict(element_bytes=32)
+        variants["keep_base_element_bytes_32_sweep"] = dict(keep_base=True, element_bytes=32)
+    for name, kw in variants.items():
+        if args.keep_base and kw.get("keep_base") and "element_bytes" not in kw:
+            continue
+        pk = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, nblk=args.nblk, tile=args.tile,
+                  **kw)
+        ok = [torch.empty_like(o) for o in outs]
+        msk = time_events(lambda: pk.sweep(F, ok, graph=True), reps, stream)
+        same = all(torch.equal(a, b) for a, b in zip(ok, outs))
+        res[name] = {"ms_per_sweep": msk, "outputs_equal_default_plan": same}
+        pk.close()
+        del ok
     # one CP-ALS iteration (FP64 Gram/Cholesky on the GPU), replayed as a CUDA graph
     Fa = [f.clone() for f in F]
     lam = torch.empty(R, device=dev)
@@ -344,7 +364,8 @@ def main():
     t0 = time.perf_counter()
     plan = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, nblk=args.nblk, tile=args.tile,
                 variant=args.variant, unroll=args.unroll, cache_hints=args.hints,
-                stages=args.stages, element_bytes=args.element_bytes)
+                stages=args.stages, element_bytes=args.element_bytes,
+                keep_base=args.keep_base)
     plan_s = time.perf_counter() - t0
     info = plan.info()
     outs = [torch.empty(d, R, device=dev) for d in spec.dims]
@@ -384,7 +405,7 @@ def main():
     ms = max_over_ranks(ms, world)
 
     peak, peak_kind = load_peaks()
-    byts = compulsory_bytes(spec.dims, nnz, R, s, touched, N)
+    byts = compulsory_bytes(spec.dims, nnz, R, s, touched, N, args.keep_base)
     t_roof_ms = sum(byts) / (peak * 1e9) * 1e3
     achieved = sum(byts) / (per_mode.sum() * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload, R, args.dtype)
@@ -444,6 +465,7 @@ def main():
                        "unroll": args.unroll or 8, "cache_hints": args.hints,
                        "stages": args.stages or 3,
                        "element_bytes": info["elem_bytes"],
+                       "keep_base": bool(args.keep_base),
                        "l2": "inputs larger than L2 (element stream "
                              f"{nnz * info['elem_bytes'] / 1e9:.2f} GB per mode)",
                        "parallelism": f"replicas x{world}"},
@@ -453,7 +475,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                         "kernel": "mttkrp_remap_kernel (+ splitrow_fixup, per-mode events)",
+                         "kernel": "mttkrp_warp_kernel (+ splitrow_fixup, per-mode events)",
                          "algorithmic_bytes_per_sweep": int(sum(byts))},
             "cpu_baseline": cpu,
             "e2e": e2e,

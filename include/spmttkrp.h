@@ -79,6 +79,12 @@ typedef struct {
                        nonzero stream, remap ids and remapped copy evict first;
                        bit1: factor rows evict last                               */
   void* stream;     /* cudaStream_t for all work; NULL = default stream           */
+  int keep_base;    /* 1 = keep the mode-0 copy resident and read-only next to the
+                       two working copies (one more copy of the nonzeros): mode 0
+                       reads it, and the pass of mode N-1 writes no remap, since
+                       the mode-0 order it would produce is already resident.  A
+                       sweep then does N-1 remap scatters instead of N.  0 = two
+                       copies, every pass remaps (Algorithm 3 as written).       */
 } spmttkrp_opts_t;
 
 /* Fills *opts with the defaults (FP32, contiguous split, automatic sizes). */
@@ -122,7 +128,8 @@ int spmttkrp_remap(spmttkrp_plan_t plan, int mode);
 /*
  * Mode-n spMTTKRP (Eq. 1; Algorithms 2, 4) fused with the remap of the
  * working copy into mode (n+1) mod N order (Algorithm 3).  Remaps first if the
- * copy is not in mode-n order.
+ * copy is not in mode-n order.  With opts.keep_base the pass of mode N-1 skips
+ * the remap (the resident mode-0 copy becomes the working copy).
  *   factors  host array of nmodes device pointers (the mode-n one is not read).
  *   out      device, float [dims[mode]][rank], fully overwritten (rows with no
  *            nonzero are written as zeros); must not alias a factor.
@@ -193,7 +200,8 @@ int spmttkrp_autotune(spmttkrp_plan_t plan, const void* const* factors, float* c
 enum {
   SPM_Q_INFO = 0,     /* int64[16]: nnz, nmodes, rank, elem_bytes, cur_mode, dtype,
                          tile, nblk(mode), nsplit(mode), launches per sweep,
-                         device bytes, ...                                          */
+                         device bytes, working buffer, flags (bit0 host_only, bit1
+                         variant, bit2 keep_base), SMs, |X|^2 (double), lanes      */
   SPM_Q_NEXT_POS = 1, /* int32[nnz]: next_pos of `mode`                            */
   SPM_Q_BOUNDS = 2,   /* int64[nblk+1]: block boundaries of `mode`                 */
   SPM_Q_SPLITS = 3,   /* int64[nsplit][3]: (row, first_blk, last_blk) of `mode`   */

@@ -45,7 +45,8 @@ class Opts(ctypes.Structure):
                 ("unroll", ctypes.c_int), ("stages", ctypes.c_int),
                 ("element_bytes", ctypes.c_int),
                 ("cache_hints", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p),
+                ("keep_base", ctypes.c_int)]
 
 
 _LIB = None
@@ -119,7 +120,8 @@ class Plan:
     def __init__(self, coo, vals, dims: Sequence[int], rank: int, dtype: str = "f32",
                  nblk: int = 0, tile: int = 0, max_bytes: int = 0, checks: bool = False,
                  host_only: bool = False, stream=None, variant: int = 0, unroll: int = 0,
-                 cache_hints: int = 0, stages: int = 0, element_bytes: int = 0):
+                 cache_hints: int = 0, stages: int = 0, element_bytes: int = 0,
+                 keep_base: bool = False):
         L = lib()
         coo = np.ascontiguousarray(np.asarray(coo.cpu() if hasattr(coo, "cpu") else coo,
                                               dtype=np.int64))
@@ -138,6 +140,7 @@ class Plan:
         o.variant = int(variant)
         o.unroll, o.cache_hints, o.stages = int(unroll), int(cache_hints), int(stages)
         o.element_bytes = int(element_bytes)
+        o.keep_base = int(bool(keep_base))
         o.stream = None if host_only else _stream_ptr(stream)
         d = np.asarray(self.dims, dtype=np.int64)
         h = ctypes.c_void_p()
@@ -205,6 +208,8 @@ class Plan:
                 "num_sms", "normx2", "lanes"]
         d = dict(zip(keys, buf.tolist()))
         d["normx2"] = float(buf[14:15].view(np.float64)[0])
+        flags = d["host_only"]
+        d["host_only"], d["variant"], d["keep_base"] = flags & 1, (flags >> 1) & 1, (flags >> 2) & 1
         return d
 
     def next_pos(self, mode: int) -> np.ndarray:

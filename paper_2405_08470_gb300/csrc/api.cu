@@ -97,12 +97,18 @@ static int check_factors(const spmttkrp_plan* p, const void* const* f, int skip)
 }
 
 // One remap-only pass of the working copy: mode cur_mode -> cur_mode + 1.
+// With keep_base, mode N-1 -> 0 needs no pass: the mode-0 copy is resident.
 static int remap_step(spmttkrp_plan* p) {
   const int m = p->cur_mode;
-  int st = launch_remap_only(p->d_elem[p->cur_buf], p->d_elem[1 - p->cur_buf],
-                             p->md[(size_t)m].next_pos, p->nnz, p->es, p->stream);
+  if (p->keep_base && m == p->N - 1) {
+    p->cur_mode = 0;
+    return SPM_OK;
+  }
+  const int dst = next_buf(p);
+  int st = launch_remap_only(cur_elems(p), p->d_elem[dst], p->md[(size_t)m].next_pos, p->nnz,
+                             p->es, p->stream);
   if (st) return st;
-  p->cur_buf ^= 1;
+  p->cur_buf = dst;
   p->cur_mode = (m + 1) % p->N;
   return SPM_OK;
 }
@@ -157,10 +163,13 @@ int compute_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* 
     int st = remap_step(p);
     if (st) return st;
   }
-  int st = run_mode(p, mode, factors, out, p->d_elem[p->cur_buf], p->d_elem[1 - p->cur_buf],
+  // with keep_base the last mode's pass writes no remap (mode-0 copy resident)
+  const bool last = p->keep_base && mode == p->N - 1;
+  const int dst = next_buf(p);
+  int st = run_mode(p, mode, factors, out, cur_elems(p), last ? nullptr : p->d_elem[dst],
                     nullptr);
   if (st) return st;
-  if (p->nnz > 0) p->cur_buf ^= 1;
+  if (p->nnz > 0 && !last) p->cur_buf = dst;
   p->cur_mode = (mode + 1) % p->N;
   return SPM_OK;
 }
@@ -225,6 +234,8 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     return fail(SPM_ERR_INVALID_ARG, "stages must be 0 or in [2, 4]");
   if (o.cache_hints < -1 || o.cache_hints > 3)
     return fail(SPM_ERR_INVALID_ARG, "cache_hints must be in [-1, 3]");
+  if (o.keep_base != 0 && o.keep_base != 1)
+    return fail(SPM_ERR_INVALID_ARG, "keep_base must be 0 or 1");
 
   spmttkrp_plan* p = new (std::nothrow) spmttkrp_plan();
   if (!p) return fail(SPM_ERR_OOM, "host allocation failed");
@@ -237,6 +248,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->stages = o.stages ? o.stages : 3;
   p->hints = o.cache_hints == 0 ? 3 : (o.cache_hints < 0 ? 0 : o.cache_hints);
   p->checks = o.checks;
+  p->keep_base = o.keep_base;
   p->host_only = o.host_only;
   p->max_bytes = o.max_bytes;
   p->stream = (cudaStream_t)o.stream;
@@ -279,12 +291,13 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     const size_t eb = (size_t)p->nnz * p->es;
     st = plan_dalloc(p, (void**)&p->d_elem[0], eb);
     if (!st) st = plan_dalloc(p, (void**)&p->d_elem[1], eb);
+    if (!st && p->keep_base) st = plan_dalloc(p, (void**)&p->d_base, eb);
     if (!st) st = plan_dalloc(p, (void**)&p->d_err, sizeof(int));
     if (!st) {
       cudaError_t e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
       if (e == cudaSuccess && eb)
-        e = cudaMemcpyAsync(p->d_elem[0], p->h_elems.data(), eb, cudaMemcpyHostToDevice,
-                            p->stream);
+        e = cudaMemcpyAsync(p->keep_base ? p->d_base : p->d_elem[0], p->h_elems.data(), eb,
+                            cudaMemcpyHostToDevice, p->stream);
       if (e != cudaSuccess) st = cuda_fail(e, "upload of the working copy");
     }
     for (int n = 0; n < N && !st; ++n) {
@@ -323,6 +336,7 @@ int spmttkrp_plan_destroy(spmttkrp_plan_t p) {
   for (auto& g : p->als_graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   for (int i = 0; i < 3; ++i) dfree(p->d_elem[i]);
+  dfree(p->d_base);
   for (auto& d : p->md) {
     dfree(d.next_pos);
     dfree(d.blkinfo);
@@ -427,6 +441,8 @@ int spmttkrp_sweep(spmttkrp_plan_t p, const void* const* factors, float* const* 
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(sweep)");
     GraphCache gc;
     gc.key = key;
+    gc.end_buf = buf1;
+    gc.end_mode = mode1;
     e = cudaGraphInstantiate(&gc.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(sweep)");
@@ -438,8 +454,8 @@ int spmttkrp_sweep(spmttkrp_plan_t p, const void* const* factors, float* const* 
     return p->checks ? check_device_word(p) : SPM_OK;
   }
   SPM_CUDA(cudaGraphLaunch(hit->exec, p->stream));
-  if (p->nnz > 0 && (p->N & 1)) p->cur_buf ^= 1;
-  // the start mode is unchanged after a full cycle of N modes
+  p->cur_buf = hit->end_buf;
+  p->cur_mode = hit->end_mode;
   return p->checks ? check_device_word(p) : SPM_OK;
 }
 
@@ -478,7 +494,7 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
       o[13] = p->num_sms;
       std::memcpy(&o[14], &p->normx2, 8);
       o[15] = lane_config(p->R, p->dtype, true).L;
-      o[12] = p->host_only | (p->variant << 1);
+      o[12] = p->host_only | (p->variant << 1) | (p->keep_base << 2);
       return SPM_OK;
     }
     case SPM_Q_NEXT_POS: {
@@ -522,7 +538,7 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
       } else {
         tmp.resize((size_t)nnz * p->es);
         SPM_CUDA(cudaStreamSynchronize(p->stream));
-        SPM_CUDA(cudaMemcpy(tmp.data(), p->d_elem[p->cur_buf], tmp.size(), cudaMemcpyDeviceToHost));
+        SPM_CUDA(cudaMemcpy(tmp.data(), cur_elems(p), tmp.size(), cudaMemcpyDeviceToHost));
         src = tmp.data();
       }
       uint8_t* o = (uint8_t*)dst;

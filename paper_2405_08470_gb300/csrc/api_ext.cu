@@ -177,7 +177,7 @@ int cp_als_iter(spmttkrp_plan_t p, void* const* factors, float* lambda, double* 
     if (g.key == key) hit = &g;
   if (hit) {
     SPM_CUDA(cudaGraphLaunch(hit->exec, p->stream));
-    if (p->N & 1) p->cur_buf ^= 1;
+    p->cur_buf = hit->end_buf;
   } else {
     const int buf0 = p->cur_buf;
     st = als_enqueue(p, factors, lambda);  // eager first run
@@ -204,6 +204,7 @@ int cp_als_iter(spmttkrp_plan_t p, void* const* factors, float* lambda, double* 
     if (e != cudaSuccess) return cuda_fail(e, "ALS graph capture");
     GraphCache gc;
     gc.key = key;
+    gc.end_buf = buf1;
     e = cudaGraphInstantiate(&gc.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(ALS)");
@@ -235,7 +236,7 @@ int cp_loss_fwd(spmttkrp_plan_t p, const void* const* factors, float* loss) {
   if ((st = ensure(p, (void**)&p->d_elem[2], (size_t)p->nnz * p->es))) return st;
   FactorPtrs fp;
   for (int k = 0; k < p->N; ++k) fp.p[k] = factors[k];
-  st = launch_cp_fwd(p->d_elem[p->cur_buf], p->d_elem[2], p->nnz, p->es, p->N, fp, p->R,
+  st = launch_cp_fwd(cur_elems(p), p->d_elem[2], p->nnz, p->es, p->N, fp, p->R,
                      p->dtype, p->d_red, p->red_nb, loss, p->d_scal + 2, p->stream);
   if (st) return st;
   p->res_valid = 1;
@@ -252,12 +253,15 @@ int cp_loss_bwd(spmttkrp_plan_t p, const void* const* factors, const float* grad
     if (!factors[k] || !grads[k]) return fail(SPM_ERR_INVALID_ARG, "null factor or grad");
   if (!p->res_valid) return fail(SPM_ERR_STATE, "cp_loss_bwd needs a preceding cp_loss_fwd");
   // the residual copy ping-pongs between its own buffer and the free half of
-  // the working-copy pair; N fused passes bring it back to its start order
+  // the working-copy pair (both halves are free while the resident mode-0 copy
+  // is the working copy); it is dropped afterwards, so the last pass writes no
+  // remap
   uint8_t* bufs[2] = {p->d_elem[2], p->d_elem[1 - p->cur_buf]};
   int cur = 0;
   for (int i = 0; i < p->N; ++i) {
     const int n = (p->res_mode + i) % p->N;
-    int st = run_mode(p, n, factors, grads[n], bufs[cur], bufs[1 - cur], grad_out);
+    int st = run_mode(p, n, factors, grads[n], bufs[cur], i == p->N - 1 ? nullptr : bufs[1 - cur],
+                      grad_out);
     if (st) return st;
     if (p->nnz > 0) cur ^= 1;
   }

@@ -53,6 +53,7 @@ struct ModeDev {
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> key;
+  int end_buf = 0, end_mode = 0;  // working-copy state after one replay
 };
 
 }  // namespace spm
@@ -84,6 +85,8 @@ struct spmttkrp_plan {
   uint8_t* d_elem[3] = {nullptr, nullptr, nullptr};  // working copy ping/pong + residual copy
   int cur_buf = 0;   // which of d_elem[0..1] holds the working copy
   int cur_mode = 0;  // canonical order the working copy is in
+  int keep_base = 0;             // the mode-0 copy stays resident in d_base
+  uint8_t* d_base = nullptr;     // read-only mode-0 copy (keep_base only)
   std::vector<spm::ModeDev> md;
   float* d_part = nullptr;   // split-row partials: max nblk x 2 x R
   size_t part_cap = 0;       // floats
@@ -150,5 +153,15 @@ int launch_zero_rows(float* out, int64_t rows, int R, cudaStream_t s);
 int launch_remap_only(const uint8_t* in, uint8_t* out, const int32_t* next_pos, int64_t nnz,
                       int es, cudaStream_t s);
 size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype, int stages);
+
+// The copy of the nonzeros in the working order (the resident mode-0 copy
+// when keep_base is on and the order is mode 0).
+inline uint8_t* cur_elems(const spmttkrp_plan* p) {
+  return (p->keep_base && p->cur_mode == 0) ? p->d_base : p->d_elem[p->cur_buf];
+}
+// Buffer of the pair that the next remap of the working copy writes.
+inline int next_buf(const spmttkrp_plan* p) {
+  return (p->keep_base && p->cur_mode == 0) ? 0 : 1 - p->cur_buf;
+}
 
 }  // namespace spm
