@@ -59,8 +59,8 @@ typedef struct {
   int partition;    /* 0 = contiguous split with heavy-row splitting (only one)  */
   int nblk;         /* blocks per mode (warp blocks for variant 0, CTA blocks for
                        variant 1); 0 = size-based default                         */
-  int tile;         /* nonzeros per staged warp tile: 0 (= 256 for 3 modes, less
-                       for wider elements), 32, 64, 128 or 256                    */
+  int tile;         /* nonzeros per staged warp tile: 0 (= 64 for 32-byte and
+                       wider nonzeros, 128 for 16-byte ones), 32, 64, 128 or 256 */
   size_t max_bytes; /* cap on the plan's device memory; 0 = no cap               */
   int checks;       /* 1 = synchronize and read the device error word after every
                        compute call (slow; for debugging)                         */
@@ -71,10 +71,12 @@ typedef struct {
                        per block, each lane group streams one contiguous run     */
   int unroll;       /* nonzeros in flight per lane group in form 0: 0 (= 8), 4, 8 */
   int stages;       /* tiles per warp ring in form 0: 0 (= 3), 2, 3 or 4        */
-  int element_bytes;/* stride of a stored nonzero: 0 = smallest multiple of 16
-                       bytes (16 for 3 modes, 32 for 4..7), or 32 (3 modes padded
-                       to a whole 32-byte sector, so remap stores write whole
-                       sectors)                                                   */
+  int element_bytes;/* stride of a stored nonzero (N int32 indices + FP32 value):
+                       0 = default, 32 when that fits (up to 7 modes: remap stores
+                       then write whole 32-byte sectors, and DRAM never reads an
+                       old sector to merge half of it), else the smallest multiple
+                       of 16; 16 = unpadded (up to 3 modes, half the memory);
+                       32 = padded (up to 7 modes)                                */
   int cache_hints;  /* form 0 L2 policy: -1 = none, 0 = default (= 3); bit0: the
                        nonzero stream, remap ids and remapped copy evict first;
                        bit1: factor rows evict last                               */

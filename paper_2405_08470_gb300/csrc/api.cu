@@ -253,13 +253,18 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->max_bytes = o.max_bytes;
   p->stream = (cudaStream_t)o.stream;
   p->dims.assign(dims, dims + nmodes);
-  p->es = ((4 * nmodes + 4) + 15) & ~15;
+  // a nonzero is N int32 indices and an FP32 value; by default it is stored in a
+  // whole 32-byte sector when it fits one, so that remap stores never write part
+  // of a sector (which costs DRAM a read of the old sector first)
+  const int es_min = ((4 * nmodes + 4) + 15) & ~15;
+  p->es = es_min <= 32 ? 32 : es_min;
   if (o.element_bytes != 0) {
-    if (o.element_bytes != 32 || p->es > 32) {
+    if ((o.element_bytes != 16 && o.element_bytes != 32) || o.element_bytes < es_min) {
       delete p;
-      return fail(SPM_ERR_INVALID_ARG, "element_bytes must be 0, or 32 for up to 7 modes");
+      return fail(SPM_ERR_INVALID_ARG,
+                  "element_bytes must be 0, 16 (up to 3 modes) or 32 (up to 7 modes)");
     }
-    p->es = 32;
+    p->es = o.element_bytes;
   }
   p->tile = o.tile ? o.tile : default_tile(p->es);
   // keep the staged tiles within shared memory for wide elements

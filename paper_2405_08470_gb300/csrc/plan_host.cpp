@@ -113,7 +113,10 @@ int default_nblk(int64_t nnz, int num_sms, int variant) {
 }
 
 // default nonzeros per warp tile (before rounding each group's run to an odd length)
-int default_tile(int es) { return es <= 16 ? 128 : (es <= 32 ? 128 : 64); }
+// Nonzeros per warp tile: 128 for 16-byte nonzeros, 64 for wider ones, which
+// keeps two 8-warp CTAs per SM within shared memory (a 3-stage ring of 128
+// 32-byte nonzeros per warp would leave room for one).
+int default_tile(int es) { return es <= 16 ? 128 : 64; }
 
 // Position -> index of the nonempty row holding it (ustart ascending, size nu+1).
 static inline int64_t row_index_of(const std::vector<int64_t>& ustart, int64_t pos) {

@@ -122,6 +122,27 @@ def test_host_error_paths(case, status):
     assert ei.value.status == status
 
 
+@pytest.mark.parametrize("N,eb,want", [(2, 0, 32), (3, 0, 32), (3, 16, 16), (3, 32, 32),
+                                        (4, 0, 32), (7, 0, 32), (8, 0, 48), (4, 16, None),
+                                        (3, 24, None), (8, 32, None)])
+def test_element_stride_rules(N, eb, want):
+    # default: one whole 32-byte sector per nonzero when N indices + value fit
+    dims = (4,) * N
+    coo = np.array([[i % 4] * N for i in range(3)], np.int64)
+    coo[:, 0] = [0, 1, 2]
+    vals = np.ones(3, np.float32)
+    if want is None:
+        with pytest.raises(SpmError) as ei:
+            Plan(coo, vals, dims, 4, host_only=True, element_bytes=eb)
+        assert ei.value.status == -1
+        return
+    p = Plan(coo, vals, dims, 4, host_only=True, element_bytes=eb)
+    info = p.info()
+    assert info["elem_bytes"] == want
+    assert info["tile"] == (128 if want == 16 else 64)
+    p.close()
+
+
 def test_null_pointer_and_state_errors():
     L = lib()
     assert L.spmttkrp_plan_create(None, None, None, 0, None, 3, 4, None) == -1

@@ -202,15 +202,17 @@ def test_determinism_graph_and_remap():
     p.close()
 
 
+@pytest.mark.parametrize("eb", [0, 16, 32])
 @pytest.mark.parametrize("variant,dtype,R", [(0, "f32", 32), (0, "bf16", 32), (1, "f32", 32),
-                                             (0, "f32", 17)])
-def test_padded_32_byte_elements(variant, dtype, R):
-    # 3-mode nonzeros stored in whole 32-byte sectors: same results, same remap order
+                                             (0, "f32", 17), (0, "f32", 64), (0, "bf16", 16)])
+def test_16_and_32_byte_elements(variant, dtype, R, eb):
+    # 3-mode nonzeros unpadded (16 bytes) or in whole 32-byte sectors (the default):
+    # same results, same remap order
     dims = (300, 200, 100)
     coo, vals = synth.make_coo(dims, 9000, (1.1, 1.1, 0.0), seed=R + variant)
     p, got, F, Fh = run_all_modes(coo, vals, dims, R, dtype=dtype, nblk=29, variant=variant,
-                                  element_bytes=32)
-    assert p.info()["elem_bytes"] == 32
+                                  element_bytes=eb)
+    assert p.info()["elem_bytes"] == (eb or 32)
     c, v = coo.numpy(), vals.numpy()
     for n in range(3):
         assert O.relerr(got[n], O.mttkrp(c, v, dims, Fh, n)) <= F32_TOL
