@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--element-bytes", type=int, default=0)
     ap.add_argument("--hints", type=int, default=0, help="-1 none, 0 default, 1..3 bits")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip the plan's autotuner (by default it runs, untimed, before "
+                         "the warm-up and picks blocks per SM, tile, ring depth and form)")
     ap.add_argument("--keep-base", action="store_true",
                     help="keep the mode-0 copy resident: the last mode's pass writes no remap")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -298,6 +301,8 @@ def extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, strea
     pb = Plan(coo_h, vals_h, spec.dims, R, dtype="bf16", nblk=args.nblk, tile=args.tile)
     Fb = [f.to(torch.bfloat16) for f in F]
     ob = [torch.empty_like(o) for o in outs]
+    if args.autotune:
+        pb.autotune(Fb, ob)
     msb = time_events(lambda: pb.sweep(Fb, ob, graph=True), reps, stream)
     plan.sweep(F, outs, graph=True)
     torch.cuda.synchronize()
@@ -310,21 +315,25 @@ def extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, strea
     res["cp_loss_fwd_bwd"]["bf16"] = {"nnz_per_s": nnz / (msl * 1e-3), "ms": msl}
     pb.close()
     del ob, Fb, Fbg
-    # the same FP32 sweep with the mode-0 copy kept resident (N-1 remap scatters per
-    # sweep), and with 3-mode nonzeros padded to whole 32-byte sectors
-    variants = {"keep_base_sweep": dict(keep_base=True)}
-    if len(spec.dims) == 3:
-        variants["element_bytes_32_sweep"] = dict(element_bytes=32)
-        variants["keep_base_element_bytes_32_sweep"] = dict(keep_base=True, element_bytes=32)
+    # the same sweep with the mode-0 copy kept resident (N-1 remap scatters per
+    # sweep), and with 3-mode nonzeros unpadded (16 bytes, half-sector remap stores)
+    variants = {} if args.keep_base else {"keep_base_sweep": dict(keep_base=True)}
+    if len(spec.dims) == 3 and args.element_bytes != 16:
+        variants["element_bytes_16_sweep"] = dict(element_bytes=16, keep_base=args.keep_base)
     for name, kw in variants.items():
-        if args.keep_base and kw.get("keep_base") and "element_bytes" not in kw:
-            continue
         pk = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, nblk=args.nblk, tile=args.tile,
                   **kw)
         ok = [torch.empty_like(o) for o in outs]
+        if args.autotune:
+            pk.autotune(F, ok)
         msk = time_events(lambda: pk.sweep(F, ok, graph=True), reps, stream)
-        same = all(torch.equal(a, b) for a, b in zip(ok, outs))
-        res[name] = {"ms_per_sweep": msk, "outputs_equal_default_plan": same}
+        # tuned plans may cut blocks differently (FP32 sums in another order)
+        num = sum(float(torch.linalg.vector_norm((a - b).double())) ** 2 for a, b in zip(ok, outs))
+        den = sum(float(torch.linalg.vector_norm(b.double())) ** 2 for b in outs)
+        res[name] = {"ms_per_sweep": msk, "config": {k: pk.info()[k] for k in
+                                                     ("nblk", "tile", "stages", "variant",
+                                                      "elem_bytes", "keep_base")},
+                     "normwise_diff_vs_bench_plan": (num / den) ** 0.5 if den else None}
         pk.close()
         del ok
     # one CP-ALS iteration (FP64 Gram/Cholesky on the GPU), replayed as a CUDA graph
@@ -367,8 +376,16 @@ def main():
                 stages=args.stages, element_bytes=args.element_bytes,
                 keep_base=args.keep_base)
     plan_s = time.perf_counter() - t0
-    info = plan.info()
     outs = [torch.empty(d, R, device=dev) for d in spec.dims]
+    tune_s = None
+    # an explicitly requested launch configuration is measured as given
+    args.autotune = args.autotune and not (args.nblk or args.tile or args.stages or args.variant
+                                           or args.unroll)
+    if args.autotune:
+        t0 = time.perf_counter()
+        plan.autotune(F, outs)
+        tune_s = time.perf_counter() - t0
+    info = plan.info()
     stream = torch.cuda.current_stream()
 
     # warm-up (untimed)
@@ -461,9 +478,10 @@ def main():
             "config": {"workload": spec.name, "dims": list(spec.dims), "nnz": nnz, "rank": R,
                        "factor_dtype": args.dtype, "nblk": info["nblk"], "tile": info["tile"],
                        "kernel_form": ["warp blocks, bulk-async staged tiles",
-                                       "CTA blocks, direct runs"][args.variant],
+                                       "CTA blocks, direct runs"][info["variant"]],
+                       "autotuned": bool(args.autotune),
                        "unroll": args.unroll or 8, "cache_hints": args.hints,
-                       "stages": args.stages or 3,
+                       "stages": info["stages"],
                        "element_bytes": info["elem_bytes"],
                        "keep_base": bool(args.keep_base),
                        "l2": "inputs larger than L2 (element stream "
@@ -482,6 +500,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk,
             "plan_seconds": plan_s,
+            "autotune_seconds": tune_s,
             "touched_rows": touched,
         }
         line.update(extra)

@@ -59,8 +59,8 @@ typedef struct {
   int partition;    /* 0 = contiguous split with heavy-row splitting (only one)  */
   int nblk;         /* blocks per mode (warp blocks for variant 0, CTA blocks for
                        variant 1); 0 = size-based default                         */
-  int tile;         /* nonzeros per staged warp tile: 0 (= 64 for 32-byte and
-                       wider nonzeros, 128 for 16-byte ones), 32, 64, 128 or 256 */
+  int tile;         /* nonzeros per staged warp tile: 0 (= 128, halved while two
+                       CTAs per SM would not fit), 32, 64, 128 or 256             */
   size_t max_bytes; /* cap on the plan's device memory; 0 = no cap               */
   int checks;       /* 1 = synchronize and read the device error word after every
                        compute call (slow; for debugging)                         */
@@ -70,7 +70,8 @@ typedef struct {
                        shared memory by bulk async copies (default); 1 = one CTA
                        per block, each lane group streams one contiguous run     */
   int unroll;       /* nonzeros in flight per lane group in form 0: 0 (= 8), 4, 8 */
-  int stages;       /* tiles per warp ring in form 0: 0 (= 3), 2, 3 or 4        */
+  int stages;       /* tiles per warp ring in form 0: 0 (= 2 for 32-byte and wider
+                       nonzeros, 3 for 16-byte ones), 2, 3 or 4                   */
   int element_bytes;/* stride of a stored nonzero (N int32 indices + FP32 value):
                        0 = default, 32 when that fits (up to 7 modes: remap stores
                        then write whole 32-byte sectors, and DRAM never reads an
@@ -203,7 +204,8 @@ enum {
   SPM_Q_INFO = 0,     /* int64[16]: nnz, nmodes, rank, elem_bytes, cur_mode, dtype,
                          tile, nblk(mode), nsplit(mode), launches per sweep,
                          device bytes, working buffer, flags (bit0 host_only, bit1
-                         variant, bit2 keep_base), SMs, |X|^2 (double), lanes      */
+                         variant, bit2 keep_base, bits 3-5 ring stages), SMs,
+                         |X|^2 (double), lanes                                      */
   SPM_Q_NEXT_POS = 1, /* int32[nnz]: next_pos of `mode`                            */
   SPM_Q_BOUNDS = 2,   /* int64[nblk+1]: block boundaries of `mode`                 */
   SPM_Q_SPLITS = 3,   /* int64[nsplit][3]: (row, first_blk, last_blk) of `mode`   */

@@ -210,6 +210,7 @@ class Plan:
         d["normx2"] = float(buf[14:15].view(np.float64)[0])
         flags = d["host_only"]
         d["host_only"], d["variant"], d["keep_base"] = flags & 1, (flags >> 1) & 1, (flags >> 2) & 1
+        d["stages"] = (flags >> 3) & 7
         return d
 
     def next_pos(self, mode: int) -> np.ndarray:

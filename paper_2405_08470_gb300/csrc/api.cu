@@ -245,7 +245,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->dtype = o.factor_dtype;
   p->variant = o.variant;
   p->unroll = o.unroll ? o.unroll : 8;
-  p->stages = o.stages ? o.stages : 3;
+  p->stages = o.stages;
   p->hints = o.cache_hints == 0 ? 3 : (o.cache_hints < 0 ? 0 : o.cache_hints);
   p->checks = o.checks;
   p->keep_base = o.keep_base;
@@ -266,10 +266,14 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     }
     p->es = o.element_bytes;
   }
+  // ring depth: 2 stages for 32-byte and wider nonzeros (a tile of 128 of
+  // them is 4 KB, so two in flight keep the copies ahead), 3 for 16-byte ones
+  if (!p->stages) p->stages = p->es >= 32 ? 2 : 3;
   p->tile = o.tile ? o.tile : default_tile(p->es);
-  // keep the staged tiles within shared memory for wide elements
-  while (p->tile > 32 &&
-         mttkrp_smem_bytes(p->es, p->tile, p->R, p->dtype, p->stages) > 200 * 1024)
+  // a default tile keeps two CTAs per SM (<= 110 KB each); a requested one is
+  // only cut down to what one CTA can hold
+  const size_t smem_cap = (o.tile ? 200 : 110) * 1024;
+  while (p->tile > 32 && mttkrp_smem_bytes(p->es, p->tile, p->R, p->dtype, p->stages) > smem_cap)
     p->tile /= 2;
   if (!p->host_only) {
     cudaError_t e = cudaGetDevice(&p->device);
@@ -499,7 +503,7 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
       o[13] = p->num_sms;
       std::memcpy(&o[14], &p->normx2, 8);
       o[15] = lane_config(p->R, p->dtype, true).L;
-      o[12] = p->host_only | (p->variant << 1) | (p->keep_base << 2);
+      o[12] = p->host_only | (p->variant << 1) | (p->keep_base << 2) | (p->stages << 3);
       return SPM_OK;
     }
     case SPM_Q_NEXT_POS: {

@@ -85,8 +85,8 @@ static void drop_graphs(std::vector<GraphCache>& v) {
   v.clear();
 }
 
-// Re-cuts every mode into nblk blocks and switches the kernel form / tile.
-static int apply_config(spmttkrp_plan* p, int nblk, int tile, int variant) {
+// Re-cuts every mode into nblk blocks and switches the kernel form / tile / ring.
+static int apply_config(spmttkrp_plan* p, int nblk, int tile, int variant, int stages) {
   for (int n = 0; n < p->N; ++n) {
     int st = partition_mode(p, n, nblk, &p->mh[(size_t)n]);
     if (st) return st;
@@ -95,12 +95,13 @@ static int apply_config(spmttkrp_plan* p, int nblk, int tile, int variant) {
   }
   p->tile = tile;
   p->variant = variant;
+  p->stages = stages;
   drop_graphs(p->sweep_graphs);
   drop_graphs(p->als_graphs);
   return SPM_OK;
 }
 
-// ---- autotune cache: one line per key, "key nblk_per_sm tile variant"
+// ---- autotune cache: one line per key, "key nblk_per_sm tile variant stages"
 static std::string tune_key(const spmttkrp_plan* p) {
   int64_t maxdeg = 0;
   for (int n = 0; n < p->N; ++n) {
@@ -110,12 +111,13 @@ static std::string tune_key(const spmttkrp_plan* p) {
   const int zbucket = p->nnz > 0 ? (int)std::floor(std::log2((double)p->nnz)) : 0;
   const int skew = p->nnz > 0 ? (int)std::floor(20.0 * (double)maxdeg / (double)p->nnz) : 0;
   std::ostringstream o;
-  o << "N" << p->N << "_R" << p->R << "_d" << p->dtype << "_z" << zbucket << "_s" << skew
-    << "_m" << p->num_sms;
+  o << "N" << p->N << "_R" << p->R << "_d" << p->dtype << "_e" << p->es << "_z" << zbucket
+    << "_s" << skew << "_m" << p->num_sms;
   return o.str();
 }
 
-static bool cache_lookup(const std::string& key, int* nps, int* tile, int* variant) {
+static bool cache_lookup(const std::string& key, int* nps, int* tile, int* variant,
+                         int* stages) {
   const char* path = std::getenv("SPMTTKRP_TUNE_CACHE");
   if (!path) return false;
   std::ifstream f(path);
@@ -123,18 +125,19 @@ static bool cache_lookup(const std::string& key, int* nps, int* tile, int* varia
   while (std::getline(f, line)) {
     std::istringstream is(line);
     std::string k;
-    int a, b, c;
-    if (is >> k >> a >> b >> c && k == key) {
+    int a, b, c, d;
+    if (is >> k >> a >> b >> c >> d && k == key) {
       *nps = a;
       *tile = b;
       *variant = c;
+      *stages = d;
       return true;
     }
   }
   return false;
 }
 
-static void cache_store(const std::string& key, int nps, int tile, int variant) {
+static void cache_store(const std::string& key, int nps, int tile, int variant, int stages) {
   const char* path = std::getenv("SPMTTKRP_TUNE_CACHE");
   if (!path) return;
   std::vector<std::string> keep;
@@ -149,7 +152,7 @@ static void cache_store(const std::string& key, int nps, int tile, int variant) 
   }
   std::ofstream f(path, std::ios::trunc);
   for (auto& l : keep) f << l << "\n";
-  f << key << " " << nps << " " << tile << " " << variant << "\n";
+  f << key << " " << nps << " " << tile << " " << variant << " " << stages << "\n";
 }
 
 }  // namespace spm
@@ -276,25 +279,27 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   if (!factors || !scratch) return fail(SPM_ERR_INVALID_ARG, "null argument");
   if (p->nnz == 0) return SPM_OK;
   const std::string key = tune_key(p);
-  int nps = 0, tile = 0, variant = 0;
-  if (!(flags & 1) && cache_lookup(key, &nps, &tile, &variant))
-    return apply_config(p, std::max(1, nps * p->num_sms), tile, variant);
+  int nps = 0, tile = 0, variant = 0, stages = 0;
+  if (!(flags & 1) && cache_lookup(key, &nps, &tile, &variant, &stages))
+    return apply_config(p, std::max(1, nps * p->num_sms), tile, variant, stages);
 
   struct Cand {
-    int nps, tile, variant;
+    int nps, tile, variant, stages;
   };
-  // blocks per SM: warp blocks (form 0) in multiples of 24 resident
-  // warps, CTA blocks (form 1) in multiples of 4
+  // blocks per SM: warp blocks (form 0) from 2 to 32 waves of 24 warps (each
+  // block >= 256 nonzeros), tiles whose rings keep two CTAs per SM, 2- or
+  // 3-stage rings; CTA blocks (form 1) in multiples of 4
   std::vector<Cand> cands;
-  for (int n : {24, 48, 96, 192}) {
-    if ((int64_t)n * p->num_sms * 128 > p->nnz && n > 24) continue;
-    for (int t : {128, 256})
-      if (mttkrp_smem_bytes(p->es, t, p->R, p->dtype, p->stages) <= 200 * 1024)
-        cands.push_back({n, t, 0});
+  for (int n : {48, 96, 192, 384, 768}) {
+    if ((int64_t)n * p->num_sms * 256 > p->nnz && n > 48) continue;
+    for (int t : {64, 128, 256})
+      for (int sg : {2, 3})
+        if (mttkrp_smem_bytes(p->es, t, p->R, p->dtype, sg) <= 110 * 1024)
+          cands.push_back({n, t, 0, sg});
   }
   for (int n : {4, 8, 16, 32}) {
     if ((int64_t)n * p->num_sms * 1024 > p->nnz && n > 4) continue;
-    cands.push_back({n, p->tile, 1});
+    cands.push_back({n, p->tile, 1, p->stages});
   }
   cudaEvent_t e0, e1;
   SPM_CUDA(cudaEventCreate(&e0));
@@ -303,7 +308,7 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   Cand win = cands.front();
   int st = SPM_OK;
   for (const Cand& c : cands) {
-    st = apply_config(p, std::max(1, c.nps * p->num_sms), c.tile, c.variant);
+    st = apply_config(p, std::max(1, c.nps * p->num_sms), c.tile, c.variant, c.stages);
     if (st) break;
     st = spmttkrp_sweep(p, factors, scratch, 0);  // warm
     if (st) break;
@@ -327,9 +332,9 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st) return st;
-  st = apply_config(p, std::max(1, win.nps * p->num_sms), win.tile, win.variant);
+  st = apply_config(p, std::max(1, win.nps * p->num_sms), win.tile, win.variant, win.stages);
   if (st) return st;
-  cache_store(key, win.nps, win.tile, win.variant);
+  cache_store(key, win.nps, win.tile, win.variant, win.stages);
   return SPM_OK;
 }
 

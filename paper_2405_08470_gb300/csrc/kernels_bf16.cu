@@ -30,6 +30,13 @@ int launch_mttkrp_bf16(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
   if (c.vec) {
     switch (a.nmodes) {
       case 3:
+        if (a.es == 32 && a.unroll == 4) {  // 32-byte nonzeros, 4 in flight, 3 CTAs/SM
+          switch (a.mode) {
+            case 0: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 0, 32>(a, c.L, s);
+            case 1: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 1, 32>(a, c.L, s);
+            default: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 2, 32>(a, c.L, s);
+          }
+        }
         if (a.es == 32) {  // elements padded to a full 32-byte sector
           switch (a.mode) {
             case 0: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8, 0, 32>(a, c.L, s);

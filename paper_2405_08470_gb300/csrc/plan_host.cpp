@@ -99,10 +99,11 @@ int default_nblk(int64_t nnz, int num_sms, int variant) {
   if (nnz <= 0) return 1;
   int64_t nb;
   if (variant == 0) {
-    // warp blocks: about four waves of 24 resident warps per SM, each block
-    // >= 256 nonzeros, and never more than 16K nonzeros per block
-    nb = std::max<int64_t>(std::min<int64_t>((int64_t)num_sms * 24 * 4, (nnz + 255) / 256),
-                           (nnz + 16383) / 16384);
+    // warp blocks: about 16 waves of 24 warps per SM, each block >= 256
+    // nonzeros, and never more than 4K nonzeros per block (measured: blocks of
+    // 1.7-4K nonzeros sweep fastest on 60M-200M nonzero tensors)
+    nb = std::max<int64_t>(std::min<int64_t>((int64_t)num_sms * 24 * 16, (nnz + 255) / 256),
+                           (nnz + 4095) / 4096);
   } else {
     // CTA blocks: about 32K nonzeros each, at least 4 per SM while each keeps
     // >= 256 nonzeros
@@ -112,11 +113,10 @@ int default_nblk(int64_t nnz, int num_sms, int variant) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(nb, 1 << 22));
 }
 
-// default nonzeros per warp tile (before rounding each group's run to an odd length)
-// Nonzeros per warp tile: 128 for 16-byte nonzeros, 64 for wider ones, which
-// keeps two 8-warp CTAs per SM within shared memory (a 3-stage ring of 128
-// 32-byte nonzeros per warp would leave room for one).
-int default_tile(int es) { return es <= 16 ? 128 : 64; }
+// Nonzeros per warp tile (the plan halves it while two 8-warp CTAs per SM would
+// not fit in shared memory: a 3-stage ring of 128 32-byte nonzeros per warp
+// would leave room for one, a 2-stage ring for two).
+int default_tile(int) { return 128; }
 
 // Position -> index of the nonempty row holding it (ustart ascending, size nu+1).
 static inline int64_t row_index_of(const std::vector<int64_t>& ustart, int64_t pos) {

@@ -139,7 +139,8 @@ def test_element_stride_rules(N, eb, want):
     p = Plan(coo, vals, dims, 4, host_only=True, element_bytes=eb)
     info = p.info()
     assert info["elem_bytes"] == want
-    assert info["tile"] == (128 if want == 16 else 64)
+    assert info["tile"] in (64, 128)  # 128, halved while two CTAs per SM would not fit
+    assert info["stages"] == (3 if want == 16 else 2)
     p.close()
 
 

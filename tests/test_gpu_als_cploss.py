@@ -139,6 +139,9 @@ def test_autotune_keeps_results_and_caches(tmp_path, monkeypatch):
     scratch = [torch.empty(d, R, device="cuda") for d in dims]
     p.autotune(F, scratch)
     assert cache.exists() and cache.read_text().strip()
+    key, nps, tile, variant, stages = cache.read_text().split()
+    assert "_e32_" in key and int(variant) in (0, 1) and int(stages) in (2, 3)
+    assert p.info()["tile"] == int(tile) or int(variant) == 1
     outs = [torch.full((d, R), float("nan"), device="cuda") for d in dims]
     p.sweep(F, outs)
     torch.cuda.synchronize()
