@@ -336,6 +336,27 @@ def extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, strea
                      "normwise_diff_vs_bench_plan": (num / den) ** 0.5 if den else None}
         pk.close()
         del ok
+    # the remap scatter on its own: a cycle of N remap-only passes (nonzero stream and
+    # next_pos read in order, each nonzero stored at its place in the next mode's
+    # order) against a plain device copy of the same bytes
+    N = len(spec.dims)
+    info = plan.info()
+    start = info["cur_mode"]
+
+    def remap_cycle():
+        for j in range(1, N + 1):
+            plan.remap((start + j) % N)
+
+    ms_remap = time_events(remap_cycle, reps, stream) / N
+    nbytes = nnz * info["elem_bytes"]
+    src = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    dst = torch.empty_like(src)
+    ms_copy = time_events(lambda: dst.copy_(src), reps, stream)
+    del src, dst
+    res["remap_only_pass"] = {"ms_per_mode": ms_remap, "plain_copy_same_bytes_ms": ms_copy,
+                              "elem_bytes": info["elem_bytes"],
+                              "note": "a remap pass reads and writes the same bytes as the "
+                                      "copy; the gap is the cost of scattered stores"}
     # one CP-ALS iteration (FP64 Gram/Cholesky on the GPU), replayed as a CUDA graph
     Fa = [f.clone() for f in F]
     lam = torch.empty(R, device=dev)
