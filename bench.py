@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the plan's autotuner (by default it runs, untimed, before "
                          "the warm-up and picks blocks per SM, tile, ring depth and form)")
+    ap.add_argument("--partition", type=int, default=0, choices=[0, 1],
+                    help="0: contiguous split with heavy-row splitting; 1: Algorithm 1 (LPT)")
     ap.add_argument("--keep-base", action="store_true",
                     help="keep the mode-0 copy resident: the last mode's pass writes no remap")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -395,7 +397,7 @@ def main():
     plan = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, nblk=args.nblk, tile=args.tile,
                 variant=args.variant, unroll=args.unroll, cache_hints=args.hints,
                 stages=args.stages, element_bytes=args.element_bytes,
-                keep_base=args.keep_base)
+                keep_base=args.keep_base, partition=args.partition)
     plan_s = time.perf_counter() - t0
     outs = [torch.empty(d, R, device=dev) for d in spec.dims]
     tune_s = None
@@ -505,6 +507,8 @@ def main():
                        "stages": info["stages"],
                        "element_bytes": info["elem_bytes"],
                        "keep_base": bool(args.keep_base),
+                       "partition": ["contiguous split, heavy rows split",
+                                     "Algorithm 1 (LPT), rows never split"][args.partition],
                        "l2": "inputs larger than L2 (element stream "
                              f"{nnz * info['elem_bytes'] / 1e9:.2f} GB per mode)",
                        "parallelism": f"replicas x{world}"},

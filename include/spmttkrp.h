@@ -56,7 +56,15 @@ enum spm_dtype { SPM_DTYPE_F32 = 0, SPM_DTYPE_BF16 = 1 };
 
 typedef struct {
   int factor_dtype; /* SPM_DTYPE_F32 or SPM_DTYPE_BF16 (factor storage only)     */
-  int partition;    /* 0 = contiguous split with heavy-row splitting (only one)  */
+  int partition;    /* 0 = contiguous split of each mode's order with heavy-row
+                       splitting and an ordered fix-up of split rows (default);
+                       1 = Algorithm 1 (Section 3.4): each mode's rows go, in
+                       descending degree, to the block with the fewest nonzeros
+                       so far (ties to the lowest block); the working copy of
+                       mode n is ordered by (block of i_n, K_n); no row is split
+                       (a heavy row stays in one block); rows without nonzeros
+                       are zeroed from a per-mode list; nblk (the block count
+                       kappa) is fixed when the plan is built                    */
   int nblk;         /* blocks per mode (warp blocks for variant 0, CTA blocks for
                        variant 1); 0 = size-based default                         */
   int tile;         /* nonzeros per staged warp tile: 0 (= 128, halved while two
@@ -204,7 +212,8 @@ enum {
   SPM_Q_INFO = 0,     /* int64[16]: nnz, nmodes, rank, elem_bytes, cur_mode, dtype,
                          tile, nblk(mode), nsplit(mode), launches per sweep,
                          device bytes, working buffer, flags (bit0 host_only, bit1
-                         variant, bit2 keep_base, bits 3-5 ring stages), SMs,
+                         variant, bit2 keep_base, bits 3-5 ring stages, bit6
+                         partition), SMs,
                          |X|^2 (double), lanes                                      */
   SPM_Q_NEXT_POS = 1, /* int32[nnz]: next_pos of `mode`                            */
   SPM_Q_BOUNDS = 2,   /* int64[nblk+1]: block boundaries of `mode`                 */

@@ -121,7 +121,7 @@ class Plan:
                  nblk: int = 0, tile: int = 0, max_bytes: int = 0, checks: bool = False,
                  host_only: bool = False, stream=None, variant: int = 0, unroll: int = 0,
                  cache_hints: int = 0, stages: int = 0, element_bytes: int = 0,
-                 keep_base: bool = False):
+                 keep_base: bool = False, partition: int = 0):
         L = lib()
         coo = np.ascontiguousarray(np.asarray(coo.cpu() if hasattr(coo, "cpu") else coo,
                                               dtype=np.int64))
@@ -141,6 +141,7 @@ class Plan:
         o.unroll, o.cache_hints, o.stages = int(unroll), int(cache_hints), int(stages)
         o.element_bytes = int(element_bytes)
         o.keep_base = int(bool(keep_base))
+        o.partition = int(partition)
         o.stream = None if host_only else _stream_ptr(stream)
         d = np.asarray(self.dims, dtype=np.int64)
         h = ctypes.c_void_p()
@@ -211,6 +212,7 @@ class Plan:
         flags = d["host_only"]
         d["host_only"], d["variant"], d["keep_base"] = flags & 1, (flags >> 1) & 1, (flags >> 2) & 1
         d["stages"] = (flags >> 3) & 7
+        d["partition"] = (flags >> 6) & 1
         return d
 
     def next_pos(self, mode: int) -> np.ndarray:

@@ -55,6 +55,11 @@ int upload_mode_tables(spmttkrp_plan* p, int n) {
     p->dev_bytes -= std::max<size_t>((size_t)d.nsplit * sizeof(SplitRow), 16);
     d.splits = nullptr;
   }
+  if (d.empty_rows) {
+    cudaFree(d.empty_rows);
+    p->dev_bytes -= std::max<size_t>((size_t)d.nempty * sizeof(int32_t), 16);
+    d.empty_rows = nullptr;
+  }
   d.nblk = h.nblk;
   d.nsplit = (int)h.splits.size();
   d.last_row = h.last_row;
@@ -67,6 +72,13 @@ int upload_mode_tables(spmttkrp_plan* p, int n) {
   if (d.nsplit)
     SPM_CUDA(cudaMemcpyAsync(d.splits, h.splits.data(), (size_t)d.nsplit * sizeof(SplitRow),
                              cudaMemcpyHostToDevice, p->stream));
+  d.nempty = (int)h.empty_rows.size();
+  if (d.nempty) {
+    st = plan_dalloc(p, (void**)&d.empty_rows, (size_t)d.nempty * sizeof(int32_t));
+    if (st) return st;
+    SPM_CUDA(cudaMemcpyAsync(d.empty_rows, h.empty_rows.data(), (size_t)d.nempty * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, p->stream));
+  }
   // partial-sum buffer: 2 slots of R floats per block
   size_t need = (size_t)d.nblk * 2 * p->R;
   if (need > p->part_cap) {
@@ -153,9 +165,12 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   a.hints = p->hints;
   a.unroll = p->unroll;
   a.stages = p->stages;
+  a.no_fill = p->partition == 1;
   int st = launch_mttkrp(a, p->stream);
   if (st) return st;
-  return launch_fixup(p->d_part, d.splits, d.nsplit, out, a.out_rows, p->R, scale, p->stream);
+  st = launch_fixup(p->d_part, d.splits, d.nsplit, out, a.out_rows, p->R, scale, p->stream);
+  if (st) return st;
+  return launch_zero_listed_rows(out, d.empty_rows, d.nempty, p->R, p->stream);
 }
 
 int compute_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out) {
@@ -222,8 +237,8 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   if (opts) o = *opts;
   if (o.factor_dtype != SPM_DTYPE_F32 && o.factor_dtype != SPM_DTYPE_BF16)
     return fail(SPM_ERR_INVALID_ARG, "factor_dtype must be F32 or BF16");
-  if (o.partition != 0)
-    return fail(SPM_ERR_UNSUPPORTED, "only the contiguous split (partition 0) is built");
+  if (o.partition != 0 && o.partition != 1)
+    return fail(SPM_ERR_INVALID_ARG, "partition must be 0 (contiguous split) or 1 (Algorithm 1)");
   if (o.tile != 0 && o.tile != 32 && o.tile != 64 && o.tile != 128 && o.tile != 256)
     return fail(SPM_ERR_INVALID_ARG, "tile must be 0, 32, 64, 128 or 256");
   if (o.nblk < 0) return fail(SPM_ERR_INVALID_ARG, "nblk must be >= 0");
@@ -249,6 +264,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->hints = o.cache_hints == 0 ? 3 : (o.cache_hints < 0 ? 0 : o.cache_hints);
   p->checks = o.checks;
   p->keep_base = o.keep_base;
+  p->partition = o.partition;
   p->host_only = o.host_only;
   p->max_bytes = o.max_bytes;
   p->stream = (cudaStream_t)o.stream;
@@ -350,6 +366,7 @@ int spmttkrp_plan_destroy(spmttkrp_plan_t p) {
     dfree(d.next_pos);
     dfree(d.blkinfo);
     dfree(d.splits);
+    dfree(d.empty_rows);
   }
   dfree(p->d_part);
   dfree(p->d_err);
@@ -495,7 +512,9 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
       o[7] = p->mh[(size_t)m].nblk;
       o[8] = (int64_t)p->mh[(size_t)m].splits.size();
       int64_t launches = 0;
-      for (int n = 0; n < N; ++n) launches += 1 + (p->mh[(size_t)n].splits.empty() ? 0 : 1);
+      for (int n = 0; n < N; ++n)
+        launches += 1 + (p->mh[(size_t)n].splits.empty() ? 0 : 1) +
+                    (p->mh[(size_t)n].empty_rows.empty() ? 0 : 1);
       o[9] = nnz > 0 ? launches : N;
       o[10] = (int64_t)p->dev_bytes;
       o[11] = p->cur_buf;
@@ -503,7 +522,8 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
       o[13] = p->num_sms;
       std::memcpy(&o[14], &p->normx2, 8);
       o[15] = lane_config(p->R, p->dtype, true).L;
-      o[12] = p->host_only | (p->variant << 1) | (p->keep_base << 2) | (p->stages << 3);
+      o[12] = p->host_only | (p->variant << 1) | (p->keep_base << 2) | (p->stages << 3) |
+              (p->partition << 6);
       return SPM_OK;
     }
     case SPM_Q_NEXT_POS: {

@@ -111,8 +111,8 @@ static std::string tune_key(const spmttkrp_plan* p) {
   const int zbucket = p->nnz > 0 ? (int)std::floor(std::log2((double)p->nnz)) : 0;
   const int skew = p->nnz > 0 ? (int)std::floor(20.0 * (double)maxdeg / (double)p->nnz) : 0;
   std::ostringstream o;
-  o << "N" << p->N << "_R" << p->R << "_d" << p->dtype << "_e" << p->es << "_z" << zbucket
-    << "_s" << skew << "_m" << p->num_sms;
+  o << "N" << p->N << "_R" << p->R << "_d" << p->dtype << "_e" << p->es << "_p" << p->partition
+    << "_z" << zbucket << "_s" << skew << "_m" << p->num_sms;
   return o.str();
 }
 
@@ -280,8 +280,17 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   if (p->nnz == 0) return SPM_OK;
   const std::string key = tune_key(p);
   int nps = 0, tile = 0, variant = 0, stages = 0;
+  // Algorithm 1's blocks are fixed when the plan is built (the working copy is
+  // ordered by them): only the tile, ring depth and form are tuned then
+  const bool fixed_blocks = p->partition == 1;
+  // n_per_sm < 0: the plan's size-based default block count
+  const int nblk_default = default_nblk(p->nnz, p->num_sms, 0);
+  auto nblk_for = [&](int n_per_sm) {
+    if (fixed_blocks) return p->mh[0].nblk;
+    return n_per_sm < 0 ? nblk_default : std::max(1, n_per_sm * p->num_sms);
+  };
   if (!(flags & 1) && cache_lookup(key, &nps, &tile, &variant, &stages))
-    return apply_config(p, std::max(1, nps * p->num_sms), tile, variant, stages);
+    return apply_config(p, nblk_for(nps), tile, variant, stages);
 
   struct Cand {
     int nps, tile, variant, stages;
@@ -290,8 +299,12 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   // block >= 256 nonzeros), tiles whose rings keep two CTAs per SM, 2- or
   // 3-stage rings; CTA blocks (form 1) in multiples of 4
   std::vector<Cand> cands;
-  for (int n : {48, 96, 192, 384, 768}) {
-    if ((int64_t)n * p->num_sms * 256 > p->nnz && n > 48) continue;
+  bool default_listed = false;
+  for (int n : {48, 96, 192, 384, 768}) default_listed |= n * p->num_sms == nblk_default;
+  for (int n : {-1, 48, 96, 192, 384, 768}) {
+    if (n < 0 && (default_listed || fixed_blocks)) continue;
+    if (n > 0 && (int64_t)n * p->num_sms * 256 > p->nnz && n > 48) continue;
+    if (fixed_blocks && n > 48) continue;
     for (int t : {64, 128, 256})
       for (int sg : {2, 3})
         if (mttkrp_smem_bytes(p->es, t, p->R, p->dtype, sg) <= 110 * 1024)
@@ -299,6 +312,7 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   }
   for (int n : {4, 8, 16, 32}) {
     if ((int64_t)n * p->num_sms * 1024 > p->nnz && n > 4) continue;
+    if (fixed_blocks && n > 4) continue;
     cands.push_back({n, p->tile, 1, p->stages});
   }
   cudaEvent_t e0, e1;
@@ -308,7 +322,7 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   Cand win = cands.front();
   int st = SPM_OK;
   for (const Cand& c : cands) {
-    st = apply_config(p, std::max(1, c.nps * p->num_sms), c.tile, c.variant, c.stages);
+    st = apply_config(p, nblk_for(c.nps), c.tile, c.variant, c.stages);
     if (st) break;
     st = spmttkrp_sweep(p, factors, scratch, 0);  // warm
     if (st) break;
@@ -332,7 +346,7 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st) return st;
-  st = apply_config(p, std::max(1, win.nps * p->num_sms), win.tile, win.variant, win.stages);
+  st = apply_config(p, nblk_for(win.nps), win.tile, win.variant, win.stages);
   if (st) return st;
   cache_store(key, win.nps, win.tile, win.variant, win.stages);
   return SPM_OK;

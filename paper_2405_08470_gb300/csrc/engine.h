@@ -38,6 +38,9 @@ struct ModeHost {
   std::vector<int32_t> blkinfo;    // 4 * nblk
   std::vector<SplitRow> splits;    // ascending rows
   int last_row = -1;               // row of position nnz-1
+  // partition 1 (Algorithm 1): nonzeros per block and the rows with none
+  std::vector<int64_t> lpt_load;
+  std::vector<int32_t> empty_rows;
 };
 
 // Device tables of one mode.
@@ -47,6 +50,8 @@ struct ModeDev {
   int last_row = -1;
   int4* blkinfo = nullptr;
   SplitRow* splits = nullptr;
+  int32_t* empty_rows = nullptr;  // partition 1: rows of this mode with no nonzero
+  int nempty = 0;
   int32_t* next_pos = nullptr;  // nnz (+4 padding ints)
 };
 
@@ -86,6 +91,10 @@ struct spmttkrp_plan {
   int cur_buf = 0;   // which of d_elem[0..1] holds the working copy
   int cur_mode = 0;  // canonical order the working copy is in
   int keep_base = 0;             // the mode-0 copy stays resident in d_base
+  int partition = 0;             // 0 = contiguous split, 1 = Algorithm 1 (LPT)
+  int lpt_kappa = 0;                               // partition 1: blocks per mode
+  std::vector<std::vector<int64_t>> lpt_load;      // partition 1: nonzeros per block
+  std::vector<std::vector<int32_t>> lpt_empty;     // partition 1: rows with no nonzero
   uint8_t* d_base = nullptr;     // read-only mode-0 copy (keep_base only)
   std::vector<spm::ModeDev> md;
   float* d_part = nullptr;   // split-row partials: max nblk x 2 x R
@@ -145,11 +154,14 @@ struct MttkrpArgs {
   int hints;               // bit0: streams evict_first in L2; bit1: factor rows evict_last
   int unroll;              // nonzeros in flight per lane group (4 or 8; 0 = default)
   int stages;              // tiles per warp ring of the staged form (2..4)
+  int no_fill;             // 1: blocks own non-contiguous row sets (Algorithm 1), so
+                           // no kernel writes the empty rows between its rows
 };
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
 int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* out,
                  int64_t out_rows, int R, const float* scale, cudaStream_t s);
 int launch_zero_rows(float* out, int64_t rows, int R, cudaStream_t s);
+int launch_zero_listed_rows(float* out, const int32_t* rows, int nrows, int R, cudaStream_t s);
 int launch_remap_only(const uint8_t* in, uint8_t* out, const int32_t* next_pos, int64_t nnz,
                       int es, cudaStream_t s);
 size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype, int stages);

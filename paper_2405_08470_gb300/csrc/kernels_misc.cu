@@ -88,6 +88,25 @@ __global__ void zero_kernel(float4* __restrict__ out4, float* __restrict__ out, 
     out[i] = 0.f;
 }
 
+// Zeroes the listed output rows (rows of the mode with no nonzero when blocks
+// own non-contiguous row sets): one warp per row.
+__global__ void zero_listed_rows_kernel(float* __restrict__ out, const int32_t* __restrict__ rows,
+                                        int nrows, int R) {
+  const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  float* d = out + (int64_t)rows[w] * R;
+  for (int r = lane; r < R; r += 32) d[r] = 0.f;
+}
+
+int launch_zero_listed_rows(float* out, const int32_t* rows, int nrows, int R, cudaStream_t s) {
+  if (nrows <= 0) return SPM_OK;
+  const int64_t threads = (int64_t)nrows * 32;
+  zero_listed_rows_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(out, rows, nrows, R);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "zero_listed_rows_kernel launch");
+}
+
 int launch_zero_rows(float* out, int64_t rows, int R, cudaStream_t s) {
   const int64_t n = rows * R;
   if (n <= 0) return SPM_OK;

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kThreads, 3) mttkrp_direct_kernel(const Mttkrp
     return sub + L * j;
   };
   auto zero_rows_group = [&](int64_t from, int64_t to) {
+    if (a.no_fill) return;  // Algorithm 1 blocks: empty rows are zeroed from a list
     for (int64_t z = from; z < to; ++z) {
       if constexpr (VW > 1) {
         if (sub * VW < R) {
@@ -236,14 +237,14 @@ __global__ void __launch_bounds__(kThreads, 3) mttkrp_direct_kernel(const Mttkrp
         if (c < ncc && lane + 32 * c < R) d[lane + 32 * c] = ca[c];
       return;
     }
-    for (int64_t z = (int64_t)prev + 1; z < row; ++z)
+    for (int64_t z = a.no_fill ? (int64_t)row : (int64_t)prev + 1; z < row; ++z)
 #pragma unroll
       for (int c = 0; c < CC; ++c)
         if (c < ncc && lane + 32 * c < R) out[z * R + lane + 32 * c] = 0.f;
 #pragma unroll
     for (int c = 0; c < CC; ++c)
       if (c < ncc && lane + 32 * c < R) out[(int64_t)row * R + lane + 32 * c] = ca[c] * sc;
-    if (row == a.last_row)
+    if (!a.no_fill && row == a.last_row)
       for (int64_t z = (int64_t)row + 1; z < out_rows; ++z)
 #pragma unroll
         for (int c = 0; c < CC; ++c)

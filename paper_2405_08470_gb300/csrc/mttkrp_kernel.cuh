@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
     return sub + L * j;
   };
   auto zero_rows_group = [&](int64_t from, int64_t to) {
+    if (a.no_fill) return;  // Algorithm 1 blocks: empty rows are zeroed from a list
     for (int64_t z = from; z < to; ++z) {
       if constexpr (VW > 1) {
         if (sub * VW < R) {
@@ -531,10 +532,10 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
       for (int r = lane; r < R; r += 32) d[r] = cacc[r];
       return;
     }
-    for (int64_t z = (int64_t)prev + 1; z < row; ++z)
+    for (int64_t z = a.no_fill ? (int64_t)row : (int64_t)prev + 1; z < row; ++z)
       for (int r = lane; r < R; r += 32) out[z * R + r] = 0.f;
     for (int r = lane; r < R; r += 32) out[(int64_t)row * R + r] = cacc[r] * sc;
-    if (row == a.last_row)
+    if (!a.no_fill && row == a.last_row)
       for (int64_t z = (int64_t)row + 1; z < out_rows; ++z)
         for (int r = lane; r < R; r += 32) out[z * R + r] = 0.f;
   };

@@ -18,7 +18,9 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <queue>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "engine.h"
@@ -123,6 +125,56 @@ static inline int64_t row_index_of(const std::vector<int64_t>& ustart, int64_t p
   return (int64_t)(std::upper_bound(ustart.begin(), ustart.end(), pos) - ustart.begin()) - 1;
 }
 
+// Algorithm 1 (Section 3.4): the mode's vertices (output rows) in descending
+// degree, equal degrees in ascending index, each to the block holding the fewest
+// hyperedges so far, ties to the lowest block.  blk[v] = block of row v.
+static void lpt_assign(const std::vector<int64_t>& deg, int kappa, std::vector<int32_t>& blk,
+                       std::vector<int64_t>& load) {
+  const int64_t V = (int64_t)deg.size();
+  std::vector<int32_t> order((size_t)V);
+  for (int64_t v = 0; v < V; ++v) order[(size_t)v] = (int32_t)v;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return deg[(size_t)a] > deg[(size_t)b]; });
+  using Fill = std::pair<int64_t, int32_t>;  // (hyperedges in the block, block id)
+  std::priority_queue<Fill, std::vector<Fill>, std::greater<Fill>> least;
+  for (int b = 0; b < kappa; ++b) least.push({0, b});
+  blk.assign((size_t)V, 0);
+  load.assign((size_t)kappa, 0);
+  for (int32_t v : order) {
+    const int32_t b = least.top().second;
+    least.pop();
+    blk[(size_t)v] = b;
+    load[(size_t)b] += deg[(size_t)v];
+    least.push({load[(size_t)b], b});
+  }
+}
+
+// Blocks of Algorithm 1: block b is the range of the mode order (block, K_n)
+// holding its rows; no row is split, so no block has a split head or tail and
+// no kernel fills gaps between rows (the mode's empty rows are listed).
+static int partition_mode_lpt(const spmttkrp_plan* p, int n, int nblk, ModeHost* out) {
+  if (nblk != p->lpt_kappa)
+    return fail(SPM_ERR_UNSUPPORTED, "partition 1 fixes the block count when the plan is built");
+  const std::vector<int64_t>& load = p->lpt_load[(size_t)n];
+  ModeHost m;
+  m.nblk = nblk;
+  m.bounds.assign((size_t)nblk + 1, 0);
+  for (int b = 0; b < nblk; ++b) m.bounds[(size_t)b + 1] = m.bounds[(size_t)b] + load[(size_t)b];
+  m.blkinfo.assign((size_t)nblk * 4, 0);
+  for (int b = 0; b < nblk; ++b) {
+    int32_t* bi = &m.blkinfo[(size_t)b * 4];
+    bi[0] = (int32_t)m.bounds[(size_t)b];
+    bi[1] = (int32_t)m.bounds[(size_t)b + 1];
+    bi[2] = -1;
+    bi[3] = 0;
+  }
+  m.last_row = -1;
+  m.lpt_load = load;
+  m.empty_rows = p->lpt_empty[(size_t)n];
+  *out = std::move(m);
+  return SPM_OK;
+}
+
 // Contiguous split of one mode with heavy-row splitting (the engine's reading
 // of Section 3.4 for rows heavier than a block):
 //   T = ceil(nnz / nblk); for j = 1..nblk-1, t = min(j*T, nnz), r = the row
@@ -130,6 +182,7 @@ static inline int64_t row_index_of(const std::vector<int64_t>& ustart, int64_t p
 //   end(r), whichever is nearer (ties to start).  Else: boundary t, r is split.
 int partition_mode(const spmttkrp_plan* p, int n, int nblk, ModeHost* out) {
   if (nblk < 1) return fail(SPM_ERR_INVALID_ARG, "nblk must be >= 1");
+  if (p->partition == 1) return partition_mode_lpt(p, n, nblk, out);
   const int64_t nnz = p->nnz;
   const std::vector<int64_t>& us = p->row_start[n];   // nonempty-row starts (+nnz)
   const std::vector<int64_t>& ur = p->row_start[p->N + n];  // nonempty-row ids
@@ -271,12 +324,45 @@ int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int
   });
   if (dup.load() >= 0) return fail(SPM_ERR_DUPLICATE, "duplicate coordinate in the COO input");
 
+  // The working copy's order for mode n: K_n (partition 0), or with Algorithm 1
+  // (partition 1) the nonzeros grouped by the block of their i_n, in K_n order
+  // inside a block (Section 3.4: hyperedges follow their mode-n vertex).
+  std::vector<std::vector<int32_t>> blk;
+  if (p->partition == 1) {
+    const int kappa = nblk_opt > 0 ? nblk_opt : default_nblk(nnz, p->num_sms, p->variant);
+    p->lpt_kappa = kappa;
+    p->lpt_load.assign((size_t)N, {});
+    p->lpt_empty.assign((size_t)N, {});
+    blk.assign((size_t)N, {});
+    for (int n = 0; n < N; ++n) {
+      std::vector<int64_t> deg((size_t)p->dims[n], 0);
+      for (int64_t q = 0; q < nnz; ++q) ++deg[(size_t)key[n][(size_t)q]];
+      lpt_assign(deg, kappa, blk[(size_t)n], p->lpt_load[(size_t)n]);
+      for (int64_t r = 0; r < p->dims[n]; ++r)
+        if (deg[(size_t)r] == 0) p->lpt_empty[(size_t)n].push_back((int32_t)r);
+    }
+  }
+  std::vector<int32_t> bkey;
+  auto order_of = [&](int n, const std::vector<int32_t>& kord) {
+    std::vector<int32_t> o = kord;
+    if (p->partition != 1) return o;
+    bkey.resize((size_t)nnz);
+    parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
+      for (int64_t q = b; q < e; ++q)
+        bkey[(size_t)q] = blk[(size_t)n][(size_t)key[n][(size_t)q]];
+    });
+    stable_sort_by(bkey.data(), p->lpt_kappa, o, tmp, T);
+    return o;
+  };
+
   // working copy in mode-0 order: {int32 idx[N]; float val; zero padding}
+  std::vector<int32_t> kcur = perm0;         // K_n order
+  std::vector<int32_t> cur = order_of(0, kcur);  // order of the working copy for mode n
   const int es = p->es;
   p->h_elems.assign((size_t)nnz * es, 0);
   parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
     for (int64_t q = b; q < e; ++q) {
-      int32_t x = perm0[(size_t)q];
+      int32_t x = cur[(size_t)q];
       int32_t* d = reinterpret_cast<int32_t*>(&p->h_elems[(size_t)q * es]);
       for (int k = 0; k < N; ++k) d[k] = key[k][x];
       std::memcpy(&d[N], &vals[x], 4);
@@ -286,9 +372,9 @@ int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int
   // per mode: nonempty rows and their starts, and next_pos_n
   p->row_start.assign((size_t)2 * N, {});
   p->h_next_pos.assign((size_t)N, {});
-  std::vector<int32_t> cur = perm0, inv((size_t)nnz);
+  std::vector<int32_t> inv((size_t)nnz);
   for (int n = 0; n < N; ++n) {
-    // nonempty rows of mode n in the mode-n order `cur`
+    // nonempty rows of mode n in the mode-n order `cur` (each row is contiguous)
     const int32_t* kn = key[n].data();
     std::vector<int64_t> cnt((size_t)T + 1, 0);
     parallel_slices(T, nnz, [&](int t, int64_t b, int64_t e) {
@@ -312,10 +398,11 @@ int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int
           ++c;
         }
     });
-    // next order: stable sort of the mode-n order by i_{n+1}
+    // next K order: stable sort of K_n by i_{n+1}; the next working-copy order from it
     const int nx = (n + 1) % N;
-    std::vector<int32_t> nxt = cur;
-    stable_sort_by(key[nx].data(), p->dims[nx], nxt, tmp, T);
+    std::vector<int32_t> knext = kcur;
+    stable_sort_by(key[nx].data(), p->dims[nx], knext, tmp, T);
+    std::vector<int32_t> nxt = order_of(nx, knext);
     parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
       for (int64_t q = b; q < e; ++q) inv[(size_t)nxt[(size_t)q]] = (int32_t)q;
     });
@@ -324,13 +411,15 @@ int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int
     parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
       for (int64_t q = b; q < e; ++q) np[(size_t)q] = inv[(size_t)cur[(size_t)q]];
     });
+    kcur.swap(knext);
     cur.swap(nxt);
   }
 
   // partitions
   p->mh.assign((size_t)N, ModeHost());
   for (int n = 0; n < N; ++n) {
-    int nb = nblk_opt > 0 ? nblk_opt : default_nblk(nnz, p->num_sms, p->variant);
+    int nb = p->partition == 1 ? p->lpt_kappa
+                               : (nblk_opt > 0 ? nblk_opt : default_nblk(nnz, p->num_sms, p->variant));
     int st = partition_mode(p, n, nb, &p->mh[(size_t)n]);
     if (st != SPM_OK) return st;
   }
