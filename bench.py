@@ -359,6 +359,14 @@ def extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, strea
                               "elem_bytes": info["elem_bytes"],
                               "note": "a remap pass reads and writes the same bytes as the "
                                       "copy; the gap is the cost of scattered stores"}
+    # preprocessing (plan build: sorts, remap ids, partition, upload), on the device
+    # (the bench plan) and on the host cores
+    t0 = time.perf_counter()
+    ph = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, plan_on_host=True)
+    res["plan_build_s"] = {"device_orders": args.plan_seconds,
+                           "host_orders": time.perf_counter() - t0,
+                           "host_threads": os.cpu_count()}
+    ph.close()
     # one CP-ALS iteration (FP64 Gram/Cholesky on the GPU), replayed as a CUDA graph
     Fa = [f.clone() for f in F]
     lam = torch.empty(R, device=dev)
@@ -399,6 +407,7 @@ def main():
                 stages=args.stages, element_bytes=args.element_bytes,
                 keep_base=args.keep_base, partition=args.partition)
     plan_s = time.perf_counter() - t0
+    args.plan_seconds = plan_s
     outs = [torch.empty(d, R, device=dev) for d in spec.dims]
     tune_s = None
     # an explicitly requested launch configuration is measured as given

@@ -96,6 +96,13 @@ typedef struct {
                        the mode-0 order it would produce is already resident.  A
                        sweep then does N-1 remap scatters instead of N.  0 = two
                        copies, every pass remaps (Algorithm 3 as written).       */
+  int plan_on_host; /* 0 = a device plan with partition 0 builds its orders on the
+                       device (stable LSD radix sorts of K_n, duplicate check,
+                       working copy, next_pos; temporary device memory of about
+                       5 int32 per nonzero plus the key columns, not counted in
+                       max_bytes); 1 = on the host (parallel C++ radix passes).
+                       Both give the same plan bit for bit.  Host-only plans and
+                       partition 1 always build on the host.                    */
 } spmttkrp_opts_t;
 
 /* Fills *opts with the defaults (FP32, contiguous split, automatic sizes). */

@@ -46,7 +46,8 @@ class Opts(ctypes.Structure):
                 ("element_bytes", ctypes.c_int),
                 ("cache_hints", ctypes.c_int),
                 ("stream", ctypes.c_void_p),
-                ("keep_base", ctypes.c_int)]
+                ("keep_base", ctypes.c_int),
+                ("plan_on_host", ctypes.c_int)]
 
 
 _LIB = None
@@ -121,7 +122,7 @@ class Plan:
                  nblk: int = 0, tile: int = 0, max_bytes: int = 0, checks: bool = False,
                  host_only: bool = False, stream=None, variant: int = 0, unroll: int = 0,
                  cache_hints: int = 0, stages: int = 0, element_bytes: int = 0,
-                 keep_base: bool = False, partition: int = 0):
+                 keep_base: bool = False, partition: int = 0, plan_on_host: bool = False):
         L = lib()
         coo = np.ascontiguousarray(np.asarray(coo.cpu() if hasattr(coo, "cpu") else coo,
                                               dtype=np.int64))
@@ -142,6 +143,7 @@ class Plan:
         o.element_bytes = int(element_bytes)
         o.keep_base = int(bool(keep_base))
         o.partition = int(partition)
+        o.plan_on_host = int(bool(plan_on_host))
         o.stream = None if host_only else _stream_ptr(stream)
         d = np.asarray(self.dims, dtype=np.int64)
         h = ctypes.c_void_p()

@@ -300,9 +300,15 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
       return cuda_fail(e, "cudaGetDevice");
     }
   }
+  // The orders (sorts, remap ids, working copy) are built on the device for a
+  // device plan with the contiguous split, unless the host is asked for; the
+  // partition itself always runs on the host.
+  const bool device_orders =
+      !p->host_only && p->nnz > 0 && p->partition == 0 && !o.plan_on_host;
+  std::vector<std::vector<int32_t>> keys;
   int st;
   try {
-    st = build_host_plan(p, coo, vals, o.nblk);
+    st = device_orders ? plan_keys(p, coo, vals, keys) : build_host_plan(p, coo, vals, o.nblk);
   } catch (const std::bad_alloc&) {
     st = fail(SPM_ERR_OOM, "host allocation failed while planning");
   }
@@ -320,7 +326,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     if (!st) st = plan_dalloc(p, (void**)&p->d_err, sizeof(int));
     if (!st) {
       cudaError_t e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
-      if (e == cudaSuccess && eb)
+      if (e == cudaSuccess && eb && !device_orders)
         e = cudaMemcpyAsync(p->keep_base ? p->d_base : p->d_elem[0], p->h_elems.data(), eb,
                             cudaMemcpyHostToDevice, p->stream);
       if (e != cudaSuccess) st = cuda_fail(e, "upload of the working copy");
@@ -330,13 +336,25 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
       st = plan_dalloc(p, (void**)&d.next_pos, ((size_t)p->nnz + 4) * sizeof(int32_t));
       if (!st) {
         cudaError_t e = cudaMemsetAsync(d.next_pos, 0, ((size_t)p->nnz + 4) * 4, p->stream);
-        if (e == cudaSuccess && p->nnz)
+        if (e == cudaSuccess && p->nnz && !device_orders)
           e = cudaMemcpyAsync(d.next_pos, p->h_next_pos[(size_t)n].data(),
                               (size_t)p->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "upload of next_pos");
       }
-      if (!st) st = upload_mode_tables(p, n);
     }
+    if (!st && device_orders) {
+      std::vector<int32_t*> np((size_t)N);
+      for (int n = 0; n < N; ++n) np[(size_t)n] = p->md[(size_t)n].next_pos;
+      try {
+        st = build_device_orders(p, keys, vals, p->keep_base ? p->d_base : p->d_elem[0],
+                                 np.data());
+        std::vector<std::vector<int32_t>>().swap(keys);
+        if (!st) st = plan_partitions(p, o.nblk);
+      } catch (const std::bad_alloc&) {
+        st = fail(SPM_ERR_OOM, "host allocation failed while planning");
+      }
+    }
+    for (int n = 0; n < N && !st; ++n) st = upload_mode_tables(p, n);
     if (!st) {
       cudaError_t e = cudaStreamSynchronize(p->stream);
       if (e != cudaSuccess) st = cuda_fail(e, "plan upload");

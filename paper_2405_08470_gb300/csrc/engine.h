@@ -130,6 +130,12 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // ---- host planning (plan_host.cpp) ----
 int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int nblk_opt);
+int plan_keys(spmttkrp_plan* p, const int64_t* coo, const float* vals,
+              std::vector<std::vector<int32_t>>& key);
+int plan_partitions(spmttkrp_plan* p, int nblk_opt);
+// ---- device planning (plan_device.cu) ----
+int build_device_orders(spmttkrp_plan* p, const std::vector<std::vector<int32_t>>& key,
+                        const float* vals, uint8_t* elems, int32_t* const* next_pos);
 int default_tile(int es);
 int partition_mode(const spmttkrp_plan* p, int n, int nblk, ModeHost* out);
 int default_nblk(int64_t nnz, int num_sms, int variant);

@@ -256,13 +256,13 @@ int partition_mode(const spmttkrp_plan* p, int n, int nblk, ModeHost* out) {
   return SPM_OK;
 }
 
-int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int nblk_opt) {
+// Key columns (int32, input order) with range validation, and |X|^2.
+int plan_keys(spmttkrp_plan* p, const int64_t* coo, const float* vals,
+              std::vector<std::vector<int32_t>>& key) {
   const int N = p->N;
   const int64_t nnz = p->nnz;
   const int T = pick_threads(nnz);
-
-  // key columns (int32) in input order, with range validation
-  std::vector<std::vector<int32_t>> key(N);
+  key.assign((size_t)N, {});
   for (int k = 0; k < N; ++k) key[k].resize((size_t)nnz);
   std::atomic<int64_t> bad{-1};
   parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
@@ -299,6 +299,30 @@ int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int
     for (int64_t c = 0; c < nchunk; ++c) s += part[(size_t)c];
     p->normx2 = s;
   }
+  return SPM_OK;
+}
+
+// Block tables of every mode from the row starts (partition 0) or Algorithm 1's
+// loads (partition 1).
+int plan_partitions(spmttkrp_plan* p, int nblk_opt) {
+  p->mh.assign((size_t)p->N, ModeHost());
+  for (int n = 0; n < p->N; ++n) {
+    int nb = p->partition == 1
+                 ? p->lpt_kappa
+                 : (nblk_opt > 0 ? nblk_opt : default_nblk(p->nnz, p->num_sms, p->variant));
+    int st = partition_mode(p, n, nb, &p->mh[(size_t)n]);
+    if (st != SPM_OK) return st;
+  }
+  return SPM_OK;
+}
+
+int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int nblk_opt) {
+  const int N = p->N;
+  const int64_t nnz = p->nnz;
+  const int T = pick_threads(nnz);
+  std::vector<std::vector<int32_t>> key;
+  int kst = plan_keys(p, coo, vals, key);
+  if (kst) return kst;
 
   // mode-0 order: LSD over keys i_1, i_2, ..., i_{N-1}, then i_0 (primary)
   std::vector<int32_t> perm0((size_t)nnz), tmp((size_t)nnz);
@@ -415,15 +439,7 @@ int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int
     cur.swap(nxt);
   }
 
-  // partitions
-  p->mh.assign((size_t)N, ModeHost());
-  for (int n = 0; n < N; ++n) {
-    int nb = p->partition == 1 ? p->lpt_kappa
-                               : (nblk_opt > 0 ? nblk_opt : default_nblk(nnz, p->num_sms, p->variant));
-    int st = partition_mode(p, n, nb, &p->mh[(size_t)n]);
-    if (st != SPM_OK) return st;
-  }
-  return SPM_OK;
+  return plan_partitions(p, nblk_opt);
 }
 
 }  // namespace spm
