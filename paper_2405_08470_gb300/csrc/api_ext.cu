@@ -17,7 +17,9 @@
 
 namespace spm {
 
-constexpr int kGramChunks = 256;
+// Row chunks of a Gram matrix (FP32 within a chunk, FP64 across chunks in a fixed
+// order): enough chunks to fill the GPU, at most 32 MB of partials.
+static int gram_chunks(int R) { return R <= 64 ? 1024 : (R <= 128 ? 256 : 64); }
 
 static int ensure(spmttkrp_plan* p, void** ptr, size_t bytes) {
   if (*ptr) return SPM_OK;
@@ -32,12 +34,12 @@ static int64_t max_dim(const spmttkrp_plan* p) {
 
 static int ensure_als(spmttkrp_plan* p) {
   const size_t R = (size_t)p->R, N = (size_t)p->N, I = (size_t)max_dim(p);
-  if (!p->red_nb) p->red_nb = std::max(1, p->num_sms * 2);
+  if (!p->red_nb) p->red_nb = std::max(1, p->num_sms * 8);
   int st;
   if ((st = ensure(p, (void**)&p->d_M, I * R * 4))) return st;
   if ((st = ensure(p, (void**)&p->d_U, I * R * 4))) return st;
   if ((st = ensure(p, (void**)&p->d_gram, N * R * R * 8))) return st;
-  if ((st = ensure(p, (void**)&p->d_gpart, (size_t)kGramChunks * R * R * 8))) return st;
+  if ((st = ensure(p, (void**)&p->d_gpart, (size_t)gram_chunks((int)R) * R * R * 8))) return st;
   if ((st = ensure(p, (void**)&p->d_red, (size_t)2 * p->red_nb * R * 8))) return st;
   if ((st = ensure(p, (void**)&p->d_chol, 3 * R * R * 8))) return st;
   if ((st = ensure(p, (void**)&p->d_vinv, R * R * 4))) return st;
@@ -58,7 +60,7 @@ static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda) {
   SPM_CUDA(cudaMemsetAsync(p->d_scal, 0, 8, s));
   int st;
   for (int k = 0; k < N; ++k)
-    if ((st = launch_gram(factors[k], p->dtype, p->dims[(size_t)k], R, p->d_gpart, kGramChunks,
+    if ((st = launch_gram(factors[k], p->dtype, p->dims[(size_t)k], R, p->d_gpart, gram_chunks(R),
                           p->d_gram + (size_t)k * R * R, s)))
       return st;
   std::vector<const void*> cf(factors, factors + N);
@@ -72,7 +74,7 @@ static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda) {
     if ((st = launch_als_scale(p->d_U, p->d_M, factors[n], p->dtype, lam64, I, R, mdot, status,
                                p->red_nb, s)))
       return st;
-    if ((st = launch_gram(factors[n], p->dtype, I, R, p->d_gpart, kGramChunks,
+    if ((st = launch_gram(factors[n], p->dtype, I, R, p->d_gpart, gram_chunks(R),
                           p->d_gram + (size_t)n * R * R, s)))
       return st;
   }

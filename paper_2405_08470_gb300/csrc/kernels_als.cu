@@ -49,20 +49,22 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const T* __restrict__
   const int64_t lo = (int64_t)chunk * rows_per_chunk;
   const int64_t hi = min(I, lo + rows_per_chunk);
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const bool diag = blockIdx.y == blockIdx.z;  // the two column tiles are the same
+  float(*Bs)[33] = diag ? Ar : As;
   for (int64_t base = lo; base < hi; base += 64) {
     for (int q = threadIdx.x; q < 64 * 32; q += 256) {
       const int rr = q >> 5, cc = q & 31;
       const int64_t row = base + rr;
       const bool ok = row < hi;
       Ar[rr][cc] = (ok && r0 + cc < R) ? to_f<T>(A[row * R + r0 + cc]) : 0.f;
-      As[rr][cc] = (ok && s0 + cc < R) ? to_f<T>(A[row * R + s0 + cc]) : 0.f;
+      if (!diag) As[rr][cc] = (ok && s0 + cc < R) ? to_f<T>(A[row * R + s0 + cc]) : 0.f;
     }
     __syncthreads();
 #pragma unroll 8
     for (int q = 0; q < 64; ++q) {
       const float a = Ar[q][tx];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] += a * As[q][ty + 8 * j];
+      for (int j = 0; j < 4; ++j) acc[j] += a * Bs[q][ty + 8 * j];
     }
     __syncthreads();
   }
@@ -72,13 +74,57 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const T* __restrict__
   }
 }
 
+// One warp per entry: lane l sums chunks l, l+32, ... in order, then a fixed
+// tree over the lanes (deterministic for a given chunk count).
+// R <= 32: each warp streams rows of its chunk (lane l holds A[i][l]) and adds
+// the row's outer product to 32 register accumulators (A[i][s] broadcast by
+// shuffle); the 8 warps' sums are combined in warp order.  Same chunking as the
+// tiled form, FP32 within a chunk.
+template <typename T>
+__global__ void __launch_bounds__(256) gram_warp_kernel(const T* __restrict__ A, int64_t I, int R,
+                                                        int64_t rows_per_chunk,
+                                                        double* __restrict__ part) {
+  __shared__ float red[8][32][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t lo = (int64_t)blockIdx.x * rows_per_chunk;
+  const int64_t hi = min(I, lo + rows_per_chunk);
+  float acc[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) acc[t] = 0.f;
+  constexpr int RW = 4;  // rows per warp and step (loads in flight together)
+  for (int64_t i0 = lo + w; i0 < hi; i0 += 8 * RW) {
+    float a[RW];
+#pragma unroll
+    for (int q = 0; q < RW; ++q) {
+      const int64_t i = i0 + 8 * q;
+      a[q] = (i < hi && lane < R) ? to_f<T>(A[i * R + lane]) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < RW; ++q)
+#pragma unroll
+      for (int t = 0; t < 32; ++t) acc[t] = fmaf(a[q], __shfl_sync(0xffffffffu, a[q], t), acc[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < 32; ++t) red[w][lane][t] = acc[t];
+  __syncthreads();
+  for (int q = threadIdx.x; q < R * R; q += 256) {
+    const int r = q / R, c = q % R;
+    float v = 0.f;
+    for (int k = 0; k < 8; ++k) v += red[k][r][c];
+    part[(size_t)blockIdx.x * R * R + q] = (double)v;
+  }
+}
+
 __global__ void gram_reduce_kernel(const double* __restrict__ part, int nchunk, int R,
                                    double* __restrict__ G) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (q >= R * R) return;
   double s = 0.0;
-  for (int c = 0; c < nchunk; ++c) s += part[(size_t)c * R * R + q];
-  G[q] = s;
+  for (int c = lane; c < nchunk; c += 32) s += part[(size_t)c * R * R + q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) G[q] = s;
 }
 
 // ---- V = Hadamard of the other Grams, Cholesky, V^-1 (one block, FP64)
@@ -90,6 +136,7 @@ __global__ void __launch_bounds__(256) als_prep_kernel(const double* __restrict_
   double* L = work + (size_t)R * R;
   double* Li = work + (size_t)2 * R * R;
   __shared__ int bad;
+  __shared__ double rdiag[256];  // 1 / L[j][j] (R <= 256): FP64 divides are slow
   const int tid = threadIdx.x;
   if (tid == 0) bad = *status;
   __syncthreads();
@@ -110,16 +157,18 @@ __global__ void __launch_bounds__(256) als_prep_kernel(const double* __restrict_
       if (!(d > 0.0) || !isfinite(d)) {
         bad = 1;
       } else {
-        L[(size_t)j * R + j] = sqrt(d);
+        const double l = sqrt(d);
+        L[(size_t)j * R + j] = l;
+        rdiag[j] = 1.0 / l;
       }
     }
     __syncthreads();
     if (bad) break;
-    const double ljj = L[(size_t)j * R + j];
+    const double rj = rdiag[j];
     for (int i = j + 1 + tid; i < R; i += blockDim.x) {
       double s = V[(size_t)i * R + j];
       for (int k = 0; k < j; ++k) s -= L[(size_t)i * R + k] * L[(size_t)j * R + k];
-      L[(size_t)i * R + j] = s / ljj;
+      L[(size_t)i * R + j] = s * rj;
     }
     __syncthreads();
   }
@@ -129,11 +178,11 @@ __global__ void __launch_bounds__(256) als_prep_kernel(const double* __restrict_
   }
   // L^-1 column by column (lower triangular)
   for (int c = tid; c < R; c += blockDim.x) {
-    Li[(size_t)c * R + c] = 1.0 / L[(size_t)c * R + c];
+    Li[(size_t)c * R + c] = rdiag[c];
     for (int i = c + 1; i < R; ++i) {
       double s = 0.0;
       for (int k = c; k < i; ++k) s += L[(size_t)i * R + k] * Li[(size_t)k * R + c];
-      Li[(size_t)i * R + c] = -s / L[(size_t)i * R + i];
+      Li[(size_t)i * R + c] = -s * rdiag[i];
     }
   }
   __syncthreads();
@@ -165,35 +214,53 @@ __global__ void __launch_bounds__(256) als_solve_kernel(const float* __restrict_
   float csq[CC];
 #pragma unroll
   for (int c = 0; c < CC; ++c) csq[c] = 0.f;
+  // RW rows per warp and step: their loads are in flight together
+  constexpr int RW = 4;
   const int64_t stride = (int64_t)gridDim.x * 8;
-  for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < I; i += stride) {
-    float m[CC], u[CC];
+  for (int64_t i0 = (int64_t)blockIdx.x * 8 + w; i0 < I; i0 += stride * RW) {
+    float m[RW][CC], u[RW][CC];
 #pragma unroll
-    for (int c = 0; c < CC; ++c) {
-      const int r = lane + 32 * c;
-      m[c] = r < R ? M[i * R + r] : 0.f;
-      u[c] = 0.f;
+    for (int t = 0; t < RW; ++t) {
+      const int64_t i = i0 + t * stride;
+#pragma unroll
+      for (int c = 0; c < CC; ++c) {
+        const int r = lane + 32 * c;
+        m[t][c] = (i < I && r < R) ? M[i * R + r] : 0.f;
+        u[t][c] = 0.f;
+      }
     }
 #pragma unroll
     for (int cj = 0; cj < CC; ++cj) {
       for (int jj = 0; jj < 32; ++jj) {
         const int j = cj * 32 + jj;
-        const float mj = __shfl_sync(0xffffffffu, m[cj], jj);
         if (j < R) {
+          float vj[CC];
 #pragma unroll
           for (int c = 0; c < CC; ++c) {
             const int r = lane + 32 * c;
-            if (r < R) u[c] = fmaf(mj, V[(size_t)j * R + r], u[c]);
+            vj[c] = r < R ? V[(size_t)j * R + r] : 0.f;
+          }
+#pragma unroll
+          for (int t = 0; t < RW; ++t) {
+            const float mj = __shfl_sync(0xffffffffu, m[t][cj], jj);
+#pragma unroll
+            for (int c = 0; c < CC; ++c) u[t][c] = fmaf(mj, vj[c], u[t][c]);
           }
         }
       }
     }
 #pragma unroll
-    for (int c = 0; c < CC; ++c) {
-      const int r = lane + 32 * c;
-      if (r < R) {
-        U[i * R + r] = u[c];
-        csq[c] = fmaf(u[c], u[c], csq[c]);
+    for (int t = 0; t < RW; ++t) {
+      const int64_t i = i0 + t * stride;
+      if (i < I) {
+#pragma unroll
+        for (int c = 0; c < CC; ++c) {
+          const int r = lane + 32 * c;
+          if (r < R) {
+            U[i * R + r] = u[t][c];
+            csq[c] = fmaf(u[t][c], u[t][c], csq[c]);
+          }
+        }
       }
     }
   }
@@ -207,17 +274,29 @@ __global__ void __launch_bounds__(256) als_solve_kernel(const float* __restrict_
   }
 }
 
+// Sum over nb per-block partials of column r: lane l takes blocks l, l+32, ...
+// in order, then a fixed tree over the lanes (deterministic).
+__device__ __forceinline__ double warp_column_sum(const double* __restrict__ part, int nb, int R,
+                                                  int r) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b = lane; b < nb; b += 32) s += part[(size_t)b * R + r];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+
 __global__ void als_lambda_kernel(const double* __restrict__ colsq_part, int nb, int R,
                                   double* __restrict__ lam64, float* __restrict__ lam_out,
                                   const int* __restrict__ status) {
   if (*status) return;
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // one warp per column
   if (r >= R) return;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += colsq_part[(size_t)b * R + r];
-  const double l = sqrt(s);
-  lam64[r] = l;
-  lam_out[r] = (float)l;
+  const double l = sqrt(warp_column_sum(colsq_part, nb, R, r));
+  if ((threadIdx.x & 31) == 0) {
+    lam64[r] = l;
+    lam_out[r] = (float)l;
+  }
 }
 
 // ---- A_n = U / lambda (stored as T); per-block sums of M * A_n (for <X, Y>)
@@ -239,15 +318,34 @@ __global__ void __launch_bounds__(256) als_scale_kernel(const float* __restrict_
     inv[c] = r < R ? (float)(1.0 / lam64[r]) : 0.f;
     md[c] = 0.f;
   }
+  constexpr int RW = 4;  // rows per warp and step (loads in flight together)
   const int64_t stride = (int64_t)gridDim.x * 8;
-  for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < I; i += stride) {
+  for (int64_t i0 = (int64_t)blockIdx.x * 8 + w; i0 < I; i0 += stride * RW) {
+    float uu[RW][CC], mm[RW][CC];
 #pragma unroll
-    for (int c = 0; c < CC; ++c) {
-      const int r = lane + 32 * c;
-      if (r < R) {
-        const T a = from_f<T>(U[i * R + r] * inv[c]);
-        A[i * R + r] = a;
-        md[c] = fmaf(M[i * R + r], to_f<T>(a), md[c]);
+    for (int t = 0; t < RW; ++t) {
+      const int64_t i = i0 + t * stride;
+#pragma unroll
+      for (int c = 0; c < CC; ++c) {
+        const int r = lane + 32 * c;
+        const bool ok = i < I && r < R;
+        uu[t][c] = ok ? U[i * R + r] : 0.f;
+        mm[t][c] = ok ? M[i * R + r] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < RW; ++t) {
+      const int64_t i = i0 + t * stride;
+      if (i < I) {
+#pragma unroll
+        for (int c = 0; c < CC; ++c) {
+          const int r = lane + 32 * c;
+          if (r < R) {
+            const T a = from_f<T>(uu[t][c] * inv[c]);
+            A[i * R + r] = a;
+            md[c] = fmaf(mm[t][c], to_f<T>(a), md[c]);
+          }
+        }
       }
     }
   }
@@ -278,10 +376,9 @@ __global__ void __launch_bounds__(256) als_fit_kernel(const double* __restrict__
     for (int k = 0; k < N; ++k) h *= grams[(size_t)k * R * R + q];
     y2 += lam64[r] * lam64[s] * h;
   }
-  for (int r = tid; r < R; r += 256) {
-    double m = 0.0;
-    for (int b = 0; b < nb; ++b) m += mdot_part[(size_t)b * R + r];
-    xy += lam64[r] * m;
+  for (int r = tid >> 5; r < R; r += 8) {  // one warp per column
+    const double m = warp_column_sum(mdot_part, nb, R, r);
+    if ((tid & 31) == 0) xy += lam64[r] * m;
   }
   red[tid] = y2;
   red2[tid] = xy;
@@ -301,17 +398,25 @@ __global__ void __launch_bounds__(256) als_fit_kernel(const double* __restrict__
 
 int launch_gram(const void* A, int dtype, int64_t I, int R, double* part, int max_chunks,
                 double* G, cudaStream_t s) {
-  int64_t rpc = std::max<int64_t>(2048, (I + max_chunks - 1) / max_chunks);
+  int64_t rpc = std::max<int64_t>(512, (I + max_chunks - 1) / max_chunks);
   int nchunk = (int)std::max<int64_t>(1, (I + rpc - 1) / rpc);
   const int nt = (R + 31) / 32;
   dim3 grid(nchunk, nt, nt);
-  if (dtype == SPM_DTYPE_BF16)
+  if (R <= 32) {
+    if (dtype == SPM_DTYPE_BF16)
+      gram_warp_kernel<__nv_bfloat16><<<nchunk, 256, 0, s>>>(
+          static_cast<const __nv_bfloat16*>(A), I, R, rpc, part);
+    else
+      gram_warp_kernel<float><<<nchunk, 256, 0, s>>>(static_cast<const float*>(A), I, R, rpc,
+                                                     part);
+  } else if (dtype == SPM_DTYPE_BF16) {
     gram_partial_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(
         static_cast<const __nv_bfloat16*>(A), I, R, rpc, part);
-  else
+  } else {
     gram_partial_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float*>(A), I, R, rpc,
                                                     part);
-  gram_reduce_kernel<<<(R * R + 255) / 256, 256, 0, s>>>(part, nchunk, R, G);
+  }
+  gram_reduce_kernel<<<(R * R + 7) / 8, 256, 0, s>>>(part, nchunk, R, G);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SPM_OK : cuda_fail(e, "gram kernels");
 }
@@ -350,7 +455,7 @@ int launch_als_solve(const float* M, float* U, const float* vinv, int64_t I, int
 
 int launch_als_lambda(const double* colsq, int nb, int R, double* lam64, float* lam_out,
                       const int* status, cudaStream_t s) {
-  als_lambda_kernel<<<(R + 255) / 256, 256, 0, s>>>(colsq, nb, R, lam64, lam_out, status);
+  als_lambda_kernel<<<(R + 7) / 8, 256, 0, s>>>(colsq, nb, R, lam64, lam_out, status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SPM_OK : cuda_fail(e, "als_lambda_kernel");
 }
