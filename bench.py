@@ -207,20 +207,38 @@ def ncu_traffic(workload, R, dtype):
 
 
 def cpu_oracle_sample(coo_h, vals_h, dims, R, target_s, seed):
-    """Time the FP64 oracle on the first S nonzeros (draw order) of the workload for all
-    modes; S grows until the run takes about target_s seconds."""
-    import oracle
-    F = [f.numpy() for f in synth.make_factors(dims, R, seed=seed)]
+    """The multi-threaded C FP64 oracle on the first S nonzeros (draw order) of the
+    workload, all modes: median of 3 sweeps on all host threads and on one thread.  S is
+    sized so that a one-thread sweep takes about target_s / 4 seconds."""
+    from oracle import ref_c
+    F = [f.numpy().astype(np.float64) for f in synth.make_factors(dims, R, seed=seed)]
     nnz = coo_h.shape[0]
-    S = min(nnz, 100_000)
+    N = len(dims)
+    vals64 = vals_h.astype(np.float64)
+
+    def sweep(S, threads):
+        per = []
+        for n in range(N):
+            t0 = time.perf_counter()
+            ref_c.mttkrp(coo_h[:S], vals64[:S], dims, F, n, nthreads=threads)
+            per.append(time.perf_counter() - t0)
+        return per
+
+    S = min(nnz, 200_000)
     while True:
-        t0 = time.perf_counter()
-        for n in range(len(dims)):
-            oracle.mttkrp(coo_h[:S], vals_h[:S], dims, F, n)
-        dt = time.perf_counter() - t0
-        if dt >= target_s * 0.5 or S >= nnz:
-            return S, dt
-        S = min(nnz, int(S * max(2.0, target_s / max(dt, 1e-3))))
+        dt = sum(sweep(S, 1))
+        if dt >= target_s / 8 or S >= nnz:
+            break
+        S = min(nnz, int(S * max(2.0, target_s / 4 / max(dt, 1e-3))))
+    med = lambda runs: [float(np.median([r[n] for r in runs])) for n in range(N)]  # noqa: E731
+    one = med([sweep(S, 1) for _ in range(3)])
+    allt = med([sweep(S, 0) for _ in range(3)])
+    scale = 1e3 * nnz / S
+    return {"value": sum(allt) * scale, "unit": "ms", "cores": ref_c.threads(), "kind": "oracle",
+            "sample": f"first {S} nonzeros (draw order) of the workload, all {N} modes, C FP64 "
+                      f"oracle (OpenMP, rows in parallel), median of 3, time scaled by nnz/{S}",
+            "per_mode_ms": [t * scale for t in allt],
+            "one_thread": {"value": sum(one) * scale, "per_mode_ms": [t * scale for t in one]}}
 
 
 def run_reference(args, rank, world):
@@ -230,20 +248,21 @@ def run_reference(args, rank, world):
     spec = synth.workload(args.workload)
     R = args.rank or spec.ranks[0]
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    sample_nnz = 400_000
+    sample_nnz = 4_000_000
     coo, vals = synth.make_coo(spec.dims, args.nnz or spec.nnz, spec.skew, spec.seed, device=dev) \
         if dev == "cuda" else synth.make_coo(spec.dims, sample_nnz, spec.skew, spec.seed)
     nnz_full = args.nnz or spec.nnz
     coo_h = coo[:sample_nnz].cpu().numpy()
     vals_h = vals[:sample_nnz].cpu().numpy()
-    import oracle
-    F = [f.numpy() for f in synth.make_factors(spec.dims, R, seed=synth.factor_seed(
+    from oracle import ref_c
+    F = [f.numpy().astype(np.float64) for f in synth.make_factors(spec.dims, R, seed=synth.factor_seed(
         WORKLOAD_INDEX[args.workload]))]
     N = len(spec.dims)
+    vals64 = vals_h.astype(np.float64)
 
     def step():
         for n in range(N):
-            oracle.mttkrp(coo_h, vals_h, spec.dims, F, n)
+            ref_c.mttkrp(coo_h, vals64, spec.dims, F, n)
 
     for _ in range(args.warmup):
         step()
@@ -258,9 +277,10 @@ def run_reference(args, rank, world):
         "ms_per_step": ms_full, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": spec.name, "rank": R, "nnz": nnz_full},
-        "cpu_baseline": {"value": ms_full, "unit": "ms", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": ms_full, "unit": "ms", "cores": ref_c.threads(), "kind": "oracle",
                          "sample": f"first {coo_h.shape[0]} nonzeros (draw order) of the workload, "
-                                   f"all {N} modes per step, time scaled by nnz"},
+                                   f"all {N} modes per step, C FP64 oracle (OpenMP), time scaled "
+                                   f"by nnz"},
         "e2e": {"value": ms_full, "unit": "ms", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -551,10 +571,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        S, dt = cpu_oracle_sample(coo_h, vals_h, spec.dims, R, args.cpu_seconds, fseed)
-        cpu = {"value": dt * 1e3 * nnz / S, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"first {S} nonzeros (draw order) of the workload, all {N} modes, "
-                         f"FP64 numpy oracle, time scaled by nnz/{S}"}
+        cpu = cpu_oracle_sample(coo_h, vals_h, spec.dims, R, args.cpu_seconds, fseed)
 
     launches = info["launches_per_sweep"] * K
     if rank == 0:
