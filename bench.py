@@ -427,6 +427,20 @@ def extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, strea
                               "elem_bytes": info["elem_bytes"],
                               "note": "a remap pass reads and writes the same bytes as the "
                                       "copy; the gap is the cost of scattered stores"}
+    # remap share (the split of the paper's Section 5.2): every mode once more from a
+    # copy already in its order, writing no remap, against the same modes in the sweep
+    N = len(spec.dims)
+    start = plan.info()["cur_mode"]
+    no_remap = [0.0] * N
+    for j in range(N):
+        n = (start + j) % N
+        plan.remap(n)  # untimed remap-only passes bring the copy into mode-n order
+        no_remap[n] = time_events(lambda: plan.compute(n, F, outs[n], keep_order=True), reps,
+                                  stream)
+    plan.remap(start)
+    t_sweep = time_events(lambda: plan.sweep(F, outs, graph=True), reps, stream)
+    res["remap_share"] = {"sweep_ms": t_sweep, "no_remap_per_mode_ms": no_remap,
+                          "share": 1.0 - sum(no_remap) / t_sweep}
     # preprocessing (plan build: sorts, remap ids, partition, upload), on the device
     # (the bench plan) and on the host cores
     t0 = time.perf_counter()
@@ -526,6 +540,10 @@ def main():
     t_roof_ms = sum(byts) / (peak * 1e9) * 1e3
     achieved = sum(byts) / (per_mode.sum() * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload, R, args.dtype)
+    # per-nonzero gathers counted every time (no reuse in L1/L2), for comparison
+    E = 4 * N + 4
+    no_reuse = sum(nnz * (E + 4 + E) + nnz * (N - 1) * R * s + spec.dims[n] * R * 4
+                   for n in range(N))
 
     # end to end through the public API with host buffers: H2D factors, sweep, D2H outputs
     e2e = None
@@ -601,7 +619,11 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "kernel": "mttkrp_warp_kernel (+ splitrow_fixup, per-mode events)",
-                         "algorithmic_bytes_per_sweep": int(sum(byts))},
+                         "algorithmic_bytes_per_sweep": int(sum(byts)),
+                         "no_reuse_bytes_per_sweep": int(no_reuse),
+                         "dram_gbs_ncu_bytes_over_event_time": (traffic * N / (per_mode.sum() * 1e-3) / 1e9
+                                          if traffic else None),
+                         "nominal_hbm_gbs": 7900.0},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),

@@ -155,6 +155,20 @@ int spmttkrp_remap(spmttkrp_plan_t plan, int mode);
  */
 int spmttkrp_compute(spmttkrp_plan_t plan, int mode, const void* const* factors, float* out);
 
+/* flags for spmttkrp_compute_ex */
+enum { SPM_COMPUTE_KEEP_ORDER = 1 /* write no remap: the copy stays in mode order */ };
+
+/*
+ * spmttkrp_compute with flags.  SPM_COMPUTE_KEEP_ORDER: the pass computes M_n
+ * (Eq. 1) from the copy in mode-n order and writes no remap (Algorithm 3 is
+ * skipped), so the working copy stays in mode-n order and the call can be
+ * repeated (e.g. the same mode with new factors, or timing the elementwise
+ * computation without the dynamic remap, the split of Section 5.2).  Other
+ * arguments and errors as spmttkrp_compute.
+ */
+int spmttkrp_compute_ex(spmttkrp_plan_t plan, int mode, const void* const* factors, float* out,
+                        int flags);
+
 /* flags for spmttkrp_sweep */
 enum { SPM_SWEEP_GRAPH = 1 /* replay the sweep as one captured CUDA graph */ };
 

@@ -79,6 +79,7 @@ def lib():
     L.spmttkrp_set_stream.argtypes = [P, P]
     L.spmttkrp_remap.argtypes = [P, ctypes.c_int]
     L.spmttkrp_compute.argtypes = [P, ctypes.c_int, P, P]
+    L.spmttkrp_compute_ex.argtypes = [P, ctypes.c_int, P, P, ctypes.c_int]
     L.spmttkrp_sweep.argtypes = [P, P, P, ctypes.c_int]
     L.cp_als_iter.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double)]
     L.cp_loss_fwd.argtypes = [P, P, P]
@@ -174,7 +175,13 @@ class Plan:
     def remap(self, mode: int):
         check(lib().spmttkrp_remap(self._h, int(mode)))
 
-    def compute(self, mode: int, factors, out):
+    def compute(self, mode: int, factors, out, keep_order: bool = False):
+        """Mode-n spMTTKRP into out; with keep_order the pass writes no remap and the
+        working copy stays in mode-n order."""
+        if keep_order:
+            check(lib().spmttkrp_compute_ex(self._h, int(mode), _ptrs(factors),
+                                            ctypes.c_void_p(out.data_ptr()), 1))
+            return
         check(lib().spmttkrp_compute(self._h, int(mode), _ptrs(factors),
                                      ctypes.c_void_p(out.data_ptr())))
 

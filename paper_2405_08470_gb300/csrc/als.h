@@ -28,7 +28,8 @@ int launch_cp_fwd(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N
 // api.cu
 int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
              const uint8_t* ein, uint8_t* eout, const float* scale);
-int compute_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out);
+int compute_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
+                 bool keep_order);
 int upload_mode_tables(spmttkrp_plan* p, int n);
 int plan_dalloc(spmttkrp_plan* p, void** ptr, size_t bytes);
 

@@ -173,11 +173,14 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   return launch_zero_listed_rows(out, d.empty_rows, d.nempty, p->R, p->stream);
 }
 
-int compute_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out) {
+int compute_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
+                 bool keep_order) {
   while (p->cur_mode != mode) {
     int st = remap_step(p);
     if (st) return st;
   }
+  if (keep_order)  // no remap: the working copy stays in mode order
+    return run_mode(p, mode, factors, out, cur_elems(p), nullptr, nullptr);
   // with keep_base the last mode's pass writes no remap (mode-0 copy resident)
   const bool last = p->keep_base && mode == p->N - 1;
   const int dst = next_buf(p);
@@ -193,7 +196,7 @@ static int sweep_eager(spmttkrp_plan* p, const void* const* factors, float* cons
   const int start = p->cur_mode;
   for (int i = 0; i < p->N; ++i) {
     const int n = (start + i) % p->N;
-    int st = compute_mode(p, n, factors, outs[n]);
+    int st = compute_mode(p, n, factors, outs[n], false);
     if (st) return st;
   }
   return SPM_OK;
@@ -420,17 +423,23 @@ int spmttkrp_remap(spmttkrp_plan_t p, int mode) {
   return SPM_OK;
 }
 
-int spmttkrp_compute(spmttkrp_plan_t p, int mode, const void* const* factors, float* out) {
+int spmttkrp_compute_ex(spmttkrp_plan_t p, int mode, const void* const* factors, float* out,
+                        int flags) {
   int st = check_plan(p);
   if (st) return st;
   if (mode < 0 || mode >= p->N) return fail(SPM_ERR_INVALID_ARG, "mode out of range");
+  if (flags & ~SPM_COMPUTE_KEEP_ORDER) return fail(SPM_ERR_INVALID_ARG, "unknown compute flag");
   st = check_factors(p, factors, mode);
   if (st) return st;
   if (!out) return fail(SPM_ERR_INVALID_ARG, "out is null");
-  st = compute_mode(p, mode, factors, out);
+  st = compute_mode(p, mode, factors, out, (flags & SPM_COMPUTE_KEEP_ORDER) != 0);
   if (st) return st;
   if (p->checks) return check_device_word(p);
   return SPM_OK;
+}
+
+int spmttkrp_compute(spmttkrp_plan_t p, int mode, const void* const* factors, float* out) {
+  return spmttkrp_compute_ex(p, mode, factors, out, 0);
 }
 
 int spmttkrp_sweep(spmttkrp_plan_t p, const void* const* factors, float* const* outs,

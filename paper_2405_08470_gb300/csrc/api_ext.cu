@@ -66,7 +66,7 @@ static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda) {
   std::vector<const void*> cf(factors, factors + N);
   for (int n = 0; n < N; ++n) {
     const int64_t I = p->dims[(size_t)n];
-    if ((st = compute_mode(p, n, cf.data(), p->d_M))) return st;
+    if ((st = compute_mode(p, n, cf.data(), p->d_M, false))) return st;
     if ((st = launch_als_prep(p->d_gram, N, n, R, p->d_chol, p->d_vinv, status, s))) return st;
     if ((st = launch_als_solve(p->d_M, p->d_U, p->d_vinv, I, R, colsq, status, p->red_nb, s)))
       return st;

@@ -221,3 +221,28 @@ def test_16_and_32_byte_elements(variant, dtype, R, eb):
         idx, _ = p.elements()
         assert np.array_equal(idx, O.elements_in_order(c, v, m)[0])
     p.close()
+
+
+@pytest.mark.parametrize("keep_base", [False, True])
+def test_compute_keep_order(keep_base):
+    # a pass that writes no remap: same output, the copy stays in the mode's order
+    dims = (300, 200, 100)
+    coo, vals = synth.make_coo(dims, 20000, (1.1, 1.1, 0.0), seed=12)
+    c, v = coo.numpy(), vals.numpy()
+    F = [f.cuda() for f in synth.make_factors(dims, 32, seed=13)]
+    p = Plan(c, v, dims, 32, nblk=40, checks=True, keep_base=keep_base)
+    ref = [torch.empty(d, 32, device="cuda") for d in dims]
+    p.sweep(F, ref)
+    for n in (1, 2, 0, 2):
+        out = torch.full((dims[n], 32), float("nan"), device="cuda")
+        p.compute(n, F, out, keep_order=True)
+        p.compute(n, F, out, keep_order=True)   # repeatable: still in mode-n order
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref[n]), n
+        assert p.info()["cur_mode"] == n
+        assert np.array_equal(p.elements()[0], O.elements_in_order(c, v, n)[0]), n
+    out = torch.empty(dims[2], 32, device="cuda")
+    p.compute(2, F, out)                          # a plain pass remaps on to mode 0
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref[2]) and p.info()["cur_mode"] == 0
+    p.close()
