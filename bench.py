@@ -248,10 +248,10 @@ def run_reference(args, rank, world):
     spec = synth.workload(args.workload)
     R = args.rank or spec.ranks[0]
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    sample_nnz = 4_000_000
-    coo, vals = synth.make_coo(spec.dims, args.nnz or spec.nnz, spec.skew, spec.seed, device=dev) \
-        if dev == "cuda" else synth.make_coo(spec.dims, sample_nnz, spec.skew, spec.seed)
     nnz_full = args.nnz or spec.nnz
+    sample_nnz = min(4_000_000, nnz_full)
+    coo, vals = synth.make_coo(spec.dims, nnz_full, spec.skew, spec.seed, device=dev) \
+        if dev == "cuda" else synth.make_coo(spec.dims, sample_nnz, spec.skew, spec.seed)
     coo_h = coo[:sample_nnz].cpu().numpy()
     vals_h = vals[:sample_nnz].cpu().numpy()
     from oracle import ref_c
