@@ -180,12 +180,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# sources that define and launch the fused spMTTKRP + remap kernel
+KERNEL_SOURCES = ("mttkrp_common.cuh", "mttkrp_kernel.cuh", "mttkrp_direct.cuh", "kernels_f32.cu",
+                  "kernels_bf16.cu", "kernels_misc.cu")
+
+
 def kernel_digest():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2405_08470_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.startswith("mttkrp_") or f.startswith("kernels_"):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sorted(KERNEL_SOURCES):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

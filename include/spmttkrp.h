@@ -184,7 +184,7 @@ int spmttkrp_sweep(spmttkrp_plan_t plan, const void* const* factors, float* cons
                    int flags);
 
 /*
- * One CP-ALS iteration over modes 0..N-1 (Section 2.1.3; Kolda-Bader update):
+ * One CP-ALS iteration over modes 0..N-1 (Section 2.1.4; Kolda-Bader update):
  * per mode M_n = spMTTKRP, V = Hadamard of the Gram matrices A_k^T A_k (k != n)
  * in FP64, Cholesky of V in FP64, A_n = M_n V^-1, lambda = column 2-norms of
  * A_n, A_n /= lambda.  Replayed from a captured CUDA graph after the first
@@ -216,11 +216,15 @@ int cp_loss_bwd(spmttkrp_plan_t plan, const void* const* factors, const float* g
                 float* const* grads);
 
 /*
- * Chooses blocks per mode and tile size by timing all-mode sweeps with CUDA
- * events on the plan's own data, and applies the winner (deterministic
- * argmin of the median, ties to the first candidate).  Results are cached in
- * the text file named by $SPMTTKRP_TUNE_CACHE when set (one line per key:
- * "<shape key> <blocks per SM> <tile> <kernel form>").
+ * Chooses blocks per mode (2 to 32 waves of 24 warps per SM, and the size-based
+ * default), tile size, ring depth and kernel form by timing all-mode sweeps
+ * with CUDA events on the plan's own data, and applies the winner
+ * (deterministic argmin of the median of 3, ties to the first candidate).  With
+ * partition 1 the block count stays as built.  Results are cached in the text
+ * file named by $SPMTTKRP_TUNE_CACHE when set (one line per key: "<shape key>
+ * <blocks per SM, -1 = default> <tile> <kernel form> <ring depth>"); the key
+ * holds modes, rank, dtype, nonzero stride, partition, log2 nnz, the heaviest
+ * row's share and the SM count.
  *   factors  host array of nmodes device pointers used for the trial sweeps.
  *   scratch  host array of nmodes device output buffers for the trial sweeps.
  *   flags    bit 0: ignore the cache.

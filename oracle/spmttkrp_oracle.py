@@ -24,7 +24,7 @@ from typing import List, Sequence
 import numpy as np
 
 # --------------------------------------------------------------------------
-# spMTTKRP (Eq. 1, Section 2.1.3; elementwise computation, Section 2.1.5)
+# spMTTKRP (Eq. 1, Section 2.1.4; elementwise computation, Section 2.1.5)
 # --------------------------------------------------------------------------
 
 
@@ -335,7 +335,7 @@ def flycoo_bits(nnz, dims, value_bits=32):
 
 
 # --------------------------------------------------------------------------
-# CP-ALS (Section 2.1.3; the update is Kolda-Bader's, which the paper cites)
+# CP-ALS (Section 2.1.4; the update is Kolda-Bader's, which the paper cites)
 # --------------------------------------------------------------------------
 
 

@@ -1,4 +1,4 @@
-// kernels_als.cu - the CP-ALS update around the fused spMTTKRP (Section 2.1.3;
+// kernels_als.cu - the CP-ALS update around the fused spMTTKRP (Section 2.1.4;
 // the update itself is Kolda-Bader's CP-ALS, which the paper cites):
 //   G_k = A_k^T A_k            FP32 per-chunk partials, FP64 fixed-order sum
 //   V   = Hadamard_{k!=n} G_k  FP64, Cholesky V = L L^T and V^-1 in FP64
