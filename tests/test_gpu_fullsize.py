@@ -1,4 +1,4 @@
-"""Parity at the benchmark's full size, in the launch configuration bench.py times.
+"""Parity at full size, in the launch configuration bench.py times (plan defaults).
 
 The 3-mode 120000 x 90000 x 2000000 tensor with 100M Zipf(1.1) nonzeros, rank 32,
 FP32 factors, default plan options (one warp per block, staged tiles).  The FP64
@@ -6,7 +6,8 @@ oracle cannot run the whole tensor here, so it checks sampled output rows one by
 (the heaviest row of every mode, rows split over many blocks, a light row, an empty
 row when there is one, the first and the last row); the remapped working copy is
 checked by properties that hold at any size (sorted by K_0 again after the sweep,
-same multiset of nonzeros).
+same multiset of nonzeros).  The 4-mode (150M nonzeros, FP32 and BF16 factors) and
+6-mode (40M nonzeros) tensors are checked on sampled rows of at most 1M nonzeros.
 """
 import numpy as np
 import pytest
@@ -95,3 +96,63 @@ def test_full_size_sweep_sampled_rows_and_remap(c2):
     for n in range(3):
         assert torch.equal(outs[n], outs2[n])
     plan.close()
+
+
+def moderate_rows(col, dim, splits, rng, cap=1_000_000):
+    """Rows of at most `cap` nonzeros (the oracle adds a row's nonzeros one by one): a
+    split row spanning the most blocks among those, random nonempty rows, a light
+    row, an empty row, and the first and last rows when they are small enough."""
+    counts = np.bincount(col, minlength=dim)
+    ok = lambda r: counts[r] <= cap  # noqa: E731
+    rows = {r for r in (0, dim - 1) if ok(r)}
+    nz = np.nonzero((counts > 0) & (counts <= cap))[0]
+    rows.update(int(x) for x in rng.choice(nz, 4, replace=False))
+    light = np.nonzero(counts == 1)[0]
+    if light.size:
+        rows.add(int(light[0]))
+    empty = np.nonzero(counts == 0)[0]
+    if empty.size:
+        rows.add(int(empty[0]))
+    if len(splits):
+        small = [s for s in splits if ok(int(s[0]))]
+        if small:
+            rows.add(int(max(small, key=lambda s: s[2] - s[1])[0]))
+    return sorted(rows)
+
+
+@pytest.mark.parametrize("name,R,dtypes", [("c3", 32, ("f32", "bf16")), ("c4b", 32, ("f32",))])
+def test_full_size_more_modes_sampled_rows(name, R, dtypes):
+    # 4-mode 1M x 20k x 2k x 500 (150M nonzeros) and 6-mode (40M nonzeros) at full size
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    spec = synth.workload(name)
+    coo, vals = synth.make_coo(spec.dims, spec.nnz, spec.skew, spec.seed, device="cuda")
+    c, v = coo.cpu().numpy(), vals.cpu().numpy()
+    del coo, vals
+    torch.cuda.empty_cache()
+    N = len(spec.dims)
+    F = synth.make_factors(spec.dims, R, seed=synth.factor_seed(3), device="cuda")
+    rng = np.random.default_rng(1)
+    for dt in dtypes:
+        tdt = torch.bfloat16 if dt == "bf16" else torch.float32
+        Fd = [f.to(tdt) for f in F]
+        Fh = [f.float().cpu().numpy() for f in Fd]
+        plan = Plan(c, v, spec.dims, R, dtype=dt)
+        outs = [torch.full((d, R), float("nan"), device="cuda") for d in spec.dims]
+        plan.sweep(Fd, outs)
+        plan.device_status()
+        torch.cuda.synchronize()
+        for n in range(N):
+            assert not torch.isnan(outs[n]).any(), (dt, n, "unwritten rows")
+            rows = moderate_rows(c[:, n], spec.dims[n], plan.splits(n), rng)
+            want = O.mttkrp_rows(c, v, Fh, n, rows)
+            g = outs[n][rows].cpu().numpy().astype(np.float64)
+            for j, r in enumerate(rows):
+                nrm = np.linalg.norm(want[j])
+                if nrm > 0:
+                    assert np.linalg.norm(g[j] - want[j]) / nrm <= 1e-5, (dt, n, r)
+                else:
+                    assert np.all(g[j] == 0.0), (dt, n, r)
+        plan.close()
