@@ -85,7 +85,9 @@ typedef struct {
                        then write whole 32-byte sectors, and DRAM never reads an
                        old sector to merge half of it), else the smallest multiple
                        of 16; 16 = unpadded (up to 3 modes, half the memory);
-                       32 = padded (up to 7 modes)                                */
+                       32 = padded (up to 7 modes).  A 3-mode nonzero in 32 bytes
+                       carries its remap ids in the padding (Section 3.5): its
+                       positions in the three modes' orders                       */
   int cache_hints;  /* form 0 L2 policy: -1 = none, 0 = default (= 3); bit0: the
                        nonzero stream, remap ids and remapped copy evict first;
                        bit1: factor rows evict last                               */
@@ -238,7 +240,7 @@ enum {
                          tile, nblk(mode), nsplit(mode), launches per sweep,
                          device bytes, working buffer, flags (bit0 host_only, bit1
                          variant, bit2 keep_base, bits 3-5 ring stages, bit6
-                         partition), SMs,
+                         partition, bit7 nonzeros carry their remap ids), SMs,
                          |X|^2 (double), lanes                                      */
   SPM_Q_NEXT_POS = 1, /* int32[nnz]: next_pos of `mode`                            */
   SPM_Q_BOUNDS = 2,   /* int64[nblk+1]: block boundaries of `mode`                 */

@@ -222,6 +222,7 @@ class Plan:
         d["host_only"], d["variant"], d["keep_base"] = flags & 1, (flags >> 1) & 1, (flags >> 2) & 1
         d["stages"] = (flags >> 3) & 7
         d["partition"] = (flags >> 6) & 1
+        d["remap_ids_in_elements"] = (flags >> 7) & 1
         return d
 
     def next_pos(self, mode: int) -> np.ndarray:

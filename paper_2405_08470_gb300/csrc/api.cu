@@ -166,6 +166,8 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   a.unroll = p->unroll;
   a.stages = p->stages;
   a.no_fill = p->partition == 1;
+  // the pass's elements carry their remap ids: word 4 + (next mode)
+  a.alpha_word = p->alpha ? 4 + (mode + 1) % p->N : 0;
   int st = launch_mttkrp(a, p->stream);
   if (st) return st;
   st = launch_fixup(p->d_part, d.splits, d.nsplit, out, a.out_rows, p->R, scale, p->stream);
@@ -285,6 +287,9 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     }
     p->es = o.element_bytes;
   }
+  // 3-mode nonzeros in 32-byte sectors carry their remap ids in the padding (the
+  // element tuple of Section 3.5), so the fused pass reads no next_pos array
+  p->alpha = (nmodes == 3 && p->es == 32) ? 1 : 0;
   // ring depth: 2 stages for 32-byte and wider nonzeros (a tile of 128 of
   // them is 4 KB, so two in flight keep the copies ahead), 3 for 16-byte ones
   if (!p->stages) p->stages = p->es >= 32 ? 2 : 3;
@@ -550,7 +555,7 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
       std::memcpy(&o[14], &p->normx2, 8);
       o[15] = lane_config(p->R, p->dtype, true).L;
       o[12] = p->host_only | (p->variant << 1) | (p->keep_base << 2) | (p->stages << 3) |
-              (p->partition << 6);
+              (p->partition << 6) | (p->alpha << 7);
       return SPM_OK;
     }
     case SPM_Q_NEXT_POS: {

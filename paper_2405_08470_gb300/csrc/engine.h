@@ -92,6 +92,8 @@ struct spmttkrp_plan {
   int cur_mode = 0;  // canonical order the working copy is in
   int keep_base = 0;             // the mode-0 copy stays resident in d_base
   int partition = 0;             // 0 = contiguous split, 1 = Algorithm 1 (LPT)
+  int alpha = 0;  // stored nonzeros carry their remap ids: words 4..6 = position in
+                  // the mode-0/1/2 order (3 modes in 32-byte sectors)
   int lpt_kappa = 0;                               // partition 1: blocks per mode
   std::vector<std::vector<int64_t>> lpt_load;      // partition 1: nonzeros per block
   std::vector<std::vector<int32_t>> lpt_empty;     // partition 1: rows with no nonzero
@@ -162,6 +164,9 @@ struct MttkrpArgs {
   int stages;              // tiles per warp ring of the staged form (2..4)
   int no_fill;             // 1: blocks own non-contiguous row sets (Algorithm 1), so
                            // no kernel writes the empty rows between its rows
+  int alpha_word;          // > 0: int32 word of a stored nonzero holding its position in
+                           // the next mode's order (the remap id carried in the
+                           // element); 0: the next_pos array
 };
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
 int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* out,

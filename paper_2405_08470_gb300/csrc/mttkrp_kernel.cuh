@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
     const int n = max(0, min(K, gb - seg));
     uint32_t ebytes = (uint32_t)n * es, npbytes = 0;
     int np0 = 0;
-    if (remap && n > 0) {
+    if (remap && !a.alpha_word && n > 0) {  // remap ids from the next_pos array
       np0 = seg & ~3;
       npbytes = ((uint32_t)(seg + n - np0) * 4u + 15u) & ~15u;
     }
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
     if (n > 0) {
       bulk_g2s_hint(ebuf + ((size_t)st * TW + (size_t)gw * K) * es, a.elems_in + (size_t)seg * es,
                     ebytes, &mbar[st], pol_stream);
-      if (remap)
+      if (npbytes)
         bulk_g2s_hint(npbuf + (st * G + gw) * NPK, a.next_pos + np0, npbytes, &mbar[st],
                       pol_stream);
     }
@@ -481,10 +481,12 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
       const int32_t* np = npbuf + (st * G + gw) * NPK + (seg & 3);
       if (es % 32 == 0) {  // whole 32-byte sectors per store (no read of the old sector)
         const int nv = es >= 32 ? es / 32 : 1;
+        const int aw = a.alpha_word;  // remap id carried in the staged nonzero (Section 3.5)
         for (int i = sub; i < n * nv; i += L) {
           const int e = (nv == 1) ? i : i / nv, c = (nv == 1) ? 0 : i - e * nv;
           const uint4* src = reinterpret_cast<const uint4*>(eb + (size_t)e * es) + 2 * c;
-          st_hint_v8(a.elems_out + (size_t)np[e] * es + 32 * c, src[0], src[1], pol_stream);
+          const int dst = aw ? reinterpret_cast<const int*>(eb + (size_t)e * es)[aw] : np[e];
+          st_hint_v8(a.elems_out + (size_t)dst * es + 32 * c, src[0], src[1], pol_stream);
         }
       } else {
         const int nv = es / 16;  // 16-byte vectors per element (constant when NT > 0)

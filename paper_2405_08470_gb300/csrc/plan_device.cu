@@ -214,6 +214,14 @@ __global__ void fill_elems_kernel(const int32_t* __restrict__ keys, const float*
   }
 }
 
+// Remap ids carried in the stored nonzeros: word 4 + m of the nonzero at mode-0
+// position pos0[x] is x's position q in mode m's order (cur = that order).
+__global__ void alpha_fill_kernel(const int32_t* __restrict__ cur, const int32_t* __restrict__ pos0,
+                                  int64_t n, int m, uint8_t* __restrict__ elems, int es) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) reinterpret_cast<int32_t*>(elems + (int64_t)pos0[cur[q]] * es)[4 + m] = (int32_t)q;
+}
+
 __device__ __forceinline__ bool row_start_at(const int32_t* key, const int32_t* cur, int64_t q) {
   return q == 0 || key[cur[q]] != key[cur[q - 1]];
 }
@@ -322,7 +330,7 @@ int build_device_orders(spmttkrp_plan* p, const std::vector<std::vector<int32_t>
   if (n <= 0) return SPM_OK;
   if (n >= (int64_t)1 << 31) return fail(SPM_ERR_UNSUPPORTED, "device plan build: nnz >= 2^31");
   Scratch sc;
-  int32_t *d_keys, *cur, *spare, *nxt, *inv;
+  int32_t *d_keys, *cur, *spare, *nxt, *inv, *pos0 = nullptr;
   float* d_vals;
   unsigned long long* d_dup;
   Sorter so;
@@ -337,7 +345,7 @@ int build_device_orders(spmttkrp_plan* p, const std::vector<std::vector<int32_t>
       (st = sc.alloc(&so.counts, (size_t)kDigits * so.nb)) ||
       (st = sc.alloc(&so.partial, (size_t)(std::max<int64_t>((int64_t)kDigits * so.nb, n) /
                                                kScanChunk + 2))) ||
-      (st = sc.alloc(&d_dup, 1)))
+      (st = sc.alloc(&d_dup, 1)) || (p->alpha && (st = sc.alloc(&pos0, (size_t)n))))
     return st;
   for (int k = 0; k < N; ++k)
     SPM_CUDA(cudaMemcpyAsync(d_keys + (int64_t)k * n, key[(size_t)k].data(), (size_t)n * 4,
@@ -358,11 +366,13 @@ int build_device_orders(spmttkrp_plan* p, const std::vector<std::vector<int32_t>
   SPM_CUDA(cudaStreamSynchronize(s));
   if (dup != none) return fail(SPM_ERR_DUPLICATE, "duplicate coordinate in the COO input");
   fill_elems_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_keys, d_vals, n, N, cur, elems, p->es);
+  if (p->alpha) inverse_kernel<<<grid_for(n, 256), 256, 0, s>>>(cur, pos0, n);
 
   // per mode: row starts (to the host), the next order, next_pos (stays on the device)
   p->row_start.assign((size_t)2 * N, {});
   std::vector<int32_t> hs, hid;
   for (int m = 0; m < N; ++m) {
+    if (p->alpha) alpha_fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(cur, pos0, n, m, elems, p->es);
     const int32_t* km = d_keys + (int64_t)m * n;
     uint32_t* pos = so.k0;  // scratch between sorts
     row_flags_kernel<<<grid_for(n, 256), 256, 0, s>>>(km, cur, n, pos);

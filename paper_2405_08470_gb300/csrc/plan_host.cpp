@@ -393,11 +393,28 @@ int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int
     }
   });
 
+  // with p->alpha every stored nonzero also carries its remap ids: word 4 + m holds
+  // its position in mode m's order (pos0 = position in the mode-0 copy)
+  std::vector<int32_t> pos0;
+  if (p->alpha) {
+    pos0.resize((size_t)nnz);
+    parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
+      for (int64_t q = b; q < e; ++q) pos0[(size_t)cur[(size_t)q]] = (int32_t)q;
+    });
+  }
+
   // per mode: nonempty rows and their starts, and next_pos_n
   p->row_start.assign((size_t)2 * N, {});
   p->h_next_pos.assign((size_t)N, {});
   std::vector<int32_t> inv((size_t)nnz);
   for (int n = 0; n < N; ++n) {
+    if (p->alpha)
+      parallel_slices(T, nnz, [&](int, int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; ++q) {
+          int32_t* d = reinterpret_cast<int32_t*>(&p->h_elems[(size_t)pos0[(size_t)cur[(size_t)q]] * es]);
+          d[4 + n] = (int32_t)q;
+        }
+      });
     // nonempty rows of mode n in the mode-n order `cur` (each row is contiguous)
     const int32_t* kn = key[n].data();
     std::vector<int64_t> cnt((size_t)T + 1, 0);
