@@ -485,8 +485,11 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
         for (int i = sub; i < n * nv; i += L) {
           const int e = (nv == 1) ? i : i / nv, c = (nv == 1) ? 0 : i - e * nv;
           const uint4* src = reinterpret_cast<const uint4*>(eb + (size_t)e * es) + 2 * c;
-          const int dst = aw ? reinterpret_cast<const int*>(eb + (size_t)e * es)[aw] : np[e];
-          st_hint_v8(a.elems_out + (size_t)dst * es + 32 * c, src[0], src[1], pol_stream);
+          const uint4 lo = src[0], hi = src[1];
+          // with the ids in the nonzero (32-byte stride, one sector: c == 0) the id is
+          // word aw of the sector, i.e. component aw - 4 of its upper half
+          const int dst = aw ? (int)(aw == 4 ? hi.x : (aw == 5 ? hi.y : hi.z)) : np[e];
+          st_hint_v8(a.elems_out + (size_t)dst * es + 32 * c, lo, hi, pol_stream);
         }
       } else {
         const int nv = es / 16;  // 16-byte vectors per element (constant when NT > 0)
