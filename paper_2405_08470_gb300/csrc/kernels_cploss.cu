@@ -84,6 +84,109 @@ __global__ void __launch_bounds__(256) cp_fwd_kernel(const uint8_t* __restrict__
   }
 }
 
+// Batched form for 3 and 4 modes on the 16-byte-slice path: each lane group takes
+// U consecutive nonzeros at a time, issues all their factor-row slice loads before
+// using any (U * N 16-byte loads in flight per lane), reduces the U model values
+// with interleaved shuffles, and writes the U residual nonzeros with one 16-byte
+// chunk per lane.  Same products and sums per nonzero as cp_fwd_kernel; the loss is
+// accumulated per lane in a fixed order.
+template <int NT, typename T, int VW, int U>
+__global__ void __launch_bounds__(256) cp_fwd_batched_kernel(const uint8_t* __restrict__ elems,
+                                                             uint8_t* __restrict__ res,
+                                                             int64_t nnz, int es, FactorPtrs fp,
+                                                             int R, int L,
+                                                             double* __restrict__ loss_part) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int sub = lane % L, gw = lane / L, G = 32 / L;
+  const int64_t per_warp = (int64_t)G * U;
+  const int64_t wid = (int64_t)blockIdx.x * 8 + w, nw = (int64_t)gridDim.x * 8;
+  const bool lane_on = sub * VW < R;
+  const int nv = es / 16;
+  const uint64_t pol = make_policy(2);  // factor rows are reused: evict last in L2
+  double sq = 0.0;
+  for (int64_t base = wid * per_warp; base < nnz; base += nw * per_warp) {  // warp-uniform
+    int idx[U][NT];
+    float val[U];
+    bool act[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = base + (int64_t)gw * U + u;
+      act[u] = e < nnz;
+      const int* el = reinterpret_cast<const int*>(elems + (act[u] ? e : 0) * es);
+      const int4 w0 = __ldg(reinterpret_cast<const int4*>(el));
+      const int f[4] = {w0.x, w0.y, w0.z, w0.w};
+#pragma unroll
+      for (int k = 0; k < NT; ++k) idx[u][k] = k < 4 ? f[k < 4 ? k : 0] : 0;
+      val[u] = NT < 4 ? __int_as_float(f[NT < 4 ? NT : 0]) : __int_as_float(__ldg(el + NT));
+    }
+    uint4 raw[U][NT];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < NT; ++k)
+        raw[u][k] = (act[u] && lane_on)
+                        ? ld_nc_hint_v4(reinterpret_cast<const uint4*>(
+                                            static_cast<const T*>(fp.p[k]) + (int64_t)idx[u][k] * R) +
+                                            sub,
+                                        pol)
+                        : make_uint4(0u, 0u, 0u, 0u);
+    float m[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      float p[VW], x[VW];
+      Landing<T, VW, 1>::unpack(raw[u][0], p);
+#pragma unroll
+      for (int k = 1; k < NT; ++k) {
+        Landing<T, VW, 1>::unpack(raw[u][k], x);
+#pragma unroll
+        for (int j = 0; j < VW; ++j) p[j] *= x[j];
+      }
+      float t = 0.f;
+#pragma unroll
+      for (int j = 0; j < VW; ++j) t += p[j];
+      m[u] = t;
+    }
+    for (int off = L / 2; off > 0; off >>= 1)
+#pragma unroll
+      for (int u = 0; u < U; ++u) m[u] += __shfl_xor_sync(0xffffffffu, m[u], off);
+    float r[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      r[u] = m[u] - val[u];
+      if (act[u] && sub == 0) sq += (double)r[u] * (double)r[u];
+    }
+    // residual copy: chunk c of nonzero u per lane, the value word replaced by e_e
+    for (int j = sub; j < U * nv; j += L) {
+      const int u = j / nv, c = j - u * nv;
+      bool on = false;
+      float ru = 0.f;
+#pragma unroll
+      for (int q = 0; q < U; ++q)
+        if (q == u) {
+          on = act[q];
+          ru = r[q];
+        }
+      if (!on) continue;
+      const int64_t e = base + (int64_t)gw * U + u;
+      uint4 v = __ldg(reinterpret_cast<const uint4*>(elems + e * es) + c);
+      const int word = NT - 4 * c;
+      if (word == 0) v.x = __float_as_uint(ru);
+      else if (word == 1) v.y = __float_as_uint(ru);
+      else if (word == 2) v.z = __float_as_uint(ru);
+      else if (word == 3) v.w = __float_as_uint(ru);
+      reinterpret_cast<uint4*>(res + e * es)[c] = v;
+    }
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < 256; ++q) s += red[q];
+    loss_part[blockIdx.x] = s;
+  }
+}
+
 __global__ void cp_loss_final_kernel(const double* __restrict__ part, int nb,
                                      float* __restrict__ loss, double* __restrict__ loss64) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -102,9 +205,11 @@ static int fwd_dispatch(const uint8_t* elems, uint8_t* res, int64_t nnz, int es,
   constexpr int VWV = std::is_same<T, float>::value ? 4 : 8;
   if (c.vec) {
     if (N == 3)
-      cp_fwd_kernel<3, T, VWV, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part);
+      cp_fwd_batched_kernel<3, T, VWV, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, fp, R, c.L,
+                                                             part);
     else if (N == 4)
-      cp_fwd_kernel<4, T, VWV, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part);
+      cp_fwd_batched_kernel<4, T, VWV, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, fp, R, c.L,
+                                                             part);
     else
       cp_fwd_kernel<0, T, VWV, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part);
   } else {
