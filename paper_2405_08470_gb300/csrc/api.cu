@@ -62,6 +62,7 @@ int upload_mode_tables(spmttkrp_plan* p, int n) {
   }
   d.nblk = h.nblk;
   d.nsplit = (int)h.splits.size();
+  d.nchunk = h.nchunk;
   d.last_row = h.last_row;
   int st = plan_dalloc(p, (void**)&d.blkinfo, (size_t)d.nblk * sizeof(int4));
   if (st) return st;
@@ -78,6 +79,18 @@ int upload_mode_tables(spmttkrp_plan* p, int n) {
     if (st) return st;
     SPM_CUDA(cudaMemcpyAsync(d.empty_rows, h.empty_rows.data(), (size_t)d.nempty * sizeof(int32_t),
                              cudaMemcpyHostToDevice, p->stream));
+  }
+  // fix-up scratch: one R-float sum per chunk of a split row's blocks
+  const size_t fneed = (size_t)std::max(d.nchunk, 1) * p->R;
+  if (fneed > p->fixsum_cap) {
+    if (p->d_fixsum) {
+      cudaFree(p->d_fixsum);
+      p->dev_bytes -= std::max<size_t>(p->fixsum_cap * 4, 16);
+      p->d_fixsum = nullptr;
+    }
+    st = plan_dalloc(p, (void**)&p->d_fixsum, fneed * 4);
+    if (st) return st;
+    p->fixsum_cap = fneed;
   }
   // partial-sum buffer: 2 slots of R floats per block
   size_t need = (size_t)d.nblk * 2 * p->R;
@@ -170,7 +183,8 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   a.alpha_word = p->alpha ? 4 + (mode + 1) % p->N : 0;
   int st = launch_mttkrp(a, p->stream);
   if (st) return st;
-  st = launch_fixup(p->d_part, d.splits, d.nsplit, out, a.out_rows, p->R, scale, p->stream);
+  st = launch_fixup(p->d_part, d.splits, d.nsplit, d.nchunk, p->d_fixsum, out, a.out_rows, p->R,
+                    scale, p->stream);
   if (st) return st;
   return launch_zero_listed_rows(out, d.empty_rows, d.nempty, p->R, p->stream);
 }
@@ -395,6 +409,7 @@ int spmttkrp_plan_destroy(spmttkrp_plan_t p) {
     dfree(d.empty_rows);
   }
   dfree(p->d_part);
+  dfree(p->d_fixsum);
   dfree(p->d_err);
   dfree(p->d_M);
   dfree(p->d_U);
@@ -545,7 +560,7 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
       o[8] = (int64_t)p->mh[(size_t)m].splits.size();
       int64_t launches = 0;
       for (int n = 0; n < N; ++n)
-        launches += 1 + (p->mh[(size_t)n].splits.empty() ? 0 : 1) +
+        launches += 1 + (p->mh[(size_t)n].splits.empty() ? 0 : 2) +
                     (p->mh[(size_t)n].empty_rows.empty() ? 0 : 1);
       o[9] = nnz > 0 ? launches : N;
       o[10] = (int64_t)p->dev_bytes;

@@ -28,8 +28,11 @@ enum { BLK_HEAD_SPLIT = 1, BLK_TAIL_SPLIT = 2 };
 //   b = {row before this row (-1 for none), 1 if it is the last nonempty row, 0, 0}
 struct SplitRow {
   int row, first_blk, last_blk, first_slot;
-  int prev_row, is_last, pad0, pad1;
+  int prev_row, is_last;
+  int chunk0;  // the row's first chunk (of kFixChunk blocks) in the fix-up's scratch
+  int pad1;
 };
+constexpr int kFixChunk = 256;  // blocks summed by one CTA of the fix-up's first pass
 
 // Host-side result of planning one mode.
 struct ModeHost {
@@ -37,6 +40,7 @@ struct ModeHost {
   std::vector<int64_t> bounds;     // nblk + 1
   std::vector<int32_t> blkinfo;    // 4 * nblk
   std::vector<SplitRow> splits;    // ascending rows
+  int nchunk = 0;                  // fix-up chunks over all split rows
   int last_row = -1;               // row of position nnz-1
   // partition 1 (Algorithm 1): nonzeros per block and the rows with none
   std::vector<int64_t> lpt_load;
@@ -52,6 +56,7 @@ struct ModeDev {
   SplitRow* splits = nullptr;
   int32_t* empty_rows = nullptr;  // partition 1: rows of this mode with no nonzero
   int nempty = 0;
+  int nchunk = 0;                  // fix-up chunks of this mode's split rows
   int32_t* next_pos = nullptr;  // nnz (+4 padding ints)
 };
 
@@ -90,6 +95,8 @@ struct spmttkrp_plan {
   uint8_t* d_elem[3] = {nullptr, nullptr, nullptr};  // working copy ping/pong + residual copy
   int cur_buf = 0;   // which of d_elem[0..1] holds the working copy
   int cur_mode = 0;  // canonical order the working copy is in
+  float* d_fixsum = nullptr;     // fix-up scratch: one R-float sum per chunk
+  size_t fixsum_cap = 0;         // floats
   int keep_base = 0;             // the mode-0 copy stays resident in d_base
   int partition = 0;             // 0 = contiguous split, 1 = Algorithm 1 (LPT)
   int alpha = 0;  // stored nonzeros carry their remap ids: words 4..6 = position in
@@ -169,8 +176,9 @@ struct MttkrpArgs {
                            // element); 0: the next_pos array
 };
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
-int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* out,
-                 int64_t out_rows, int R, const float* scale, cudaStream_t s);
+int launch_fixup(const float* part, const SplitRow* splits, int nsplit, int nchunk,
+                 float* chunk_sums, float* out, int64_t out_rows, int R, const float* scale,
+                 cudaStream_t s);
 int launch_zero_rows(float* out, int64_t rows, int R, cudaStream_t s);
 int launch_zero_listed_rows(float* out, const int32_t* rows, int nrows, int R, cudaStream_t s);
 int launch_remap_only(const uint8_t* in, uint8_t* out, const int32_t* next_pos, int64_t nnz,

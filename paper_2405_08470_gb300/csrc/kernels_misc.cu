@@ -32,51 +32,79 @@ int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s) {
   return a.dtype == SPM_DTYPE_BF16 ? launch_mttkrp_bf16(a, c, s) : launch_mttkrp_f32(a, c, s);
 }
 
-// One CTA per split row: warp w sums the partials of blocks first_blk + w,
-// first_blk + w + 8, ... (lanes over R), the 8 warp sums are added in warp
-// order (a fixed order: results are bit-identical run to run); the empty rows
-// before the row (and after it, for the last nonempty row) are zeroed; the row
-// is written once.
-__global__ void __launch_bounds__(256) splitrow_fixup_kernel(const float* __restrict__ part,
+// Split-row fix-up in two launches, both in a fixed order (results are
+// bit-identical run to run).  Pass 1: one CTA per chunk of up to kFixChunk
+// consecutive blocks of a split row; warp w sums the chunk's blocks w, w+8, ...
+// (lanes over R) and the 8 warp sums are added in warp order.  Pass 2: one CTA
+// per split row adds its chunk sums in chunk order, writes the row once and
+// zeroes the empty rows before it (and after it, for the last nonempty row).  A
+// row spread over thousands of blocks (a Zipf head row) is summed by many CTAs.
+__global__ void __launch_bounds__(256) splitrow_chunk_kernel(const float* __restrict__ part,
                                                              const SplitRow* __restrict__ splits,
-                                                             int nsplit, float* __restrict__ out,
-                                                             int64_t out_rows, int R,
-                                                             const float* scale) {
+                                                             int nsplit, int nchunk, int R,
+                                                             float* __restrict__ chunk_sums) {
   __shared__ float red[8][kMaxRank];
-  if ((int)blockIdx.x >= nsplit) return;
-  const SplitRow sr = splits[blockIdx.x];
+  const int c = blockIdx.x;
+  if (c >= nchunk) return;
+  int lo = 0, hi = nsplit - 1;  // the split row holding chunk c: last chunk0 <= c
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (splits[mid].chunk0 <= c) lo = mid; else hi = mid - 1;
+  }
+  const SplitRow sr = splits[lo];
+  const int j = c - sr.chunk0;
+  const int b0 = sr.first_blk + j * kFixChunk;
+  const int nb = min(kFixChunk, sr.last_blk + 1 - b0);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float sc = scale ? __ldg(scale) : 1.0f;
-  const int nb = sr.last_blk - sr.first_blk + 1;
   for (int r = lane; r < R; r += 32) {
     float acc = 0.f;
     for (int i = w; i < nb; i += 8) {
-      const int b = sr.first_blk + i;
-      acc += __ldg(part + ((size_t)b * 2 + (i == 0 ? sr.first_slot : 0)) * R + r);
+      const int b = b0 + i;
+      const int slot = (b == sr.first_blk) ? sr.first_slot : 0;
+      acc += __ldg(part + ((size_t)b * 2 + slot) * R + r);
     }
     red[w][r] = acc;
-  }
-  const int64_t gap0 = (int64_t)sr.prev_row + 1, ngap = ((int64_t)sr.row - gap0) * R;
-  for (int64_t i = threadIdx.x; i < ngap; i += blockDim.x) out[gap0 * R + i] = 0.f;
-  if (sr.is_last) {
-    const int64_t t0 = (int64_t)sr.row + 1, nt = (out_rows - t0) * R;
-    for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) out[t0 * R + i] = 0.f;
   }
   __syncthreads();
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     float acc = 0.f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc += red[q][r];
+    chunk_sums[(size_t)c * R + r] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(256) splitrow_fixup_kernel(const float* __restrict__ chunk_sums,
+                                                             const SplitRow* __restrict__ splits,
+                                                             int nsplit, float* __restrict__ out,
+                                                             int64_t out_rows, int R,
+                                                             const float* scale) {
+  if ((int)blockIdx.x >= nsplit) return;
+  const SplitRow sr = splits[blockIdx.x];
+  const float sc = scale ? __ldg(scale) : 1.0f;
+  const int nc = (sr.last_blk - sr.first_blk + kFixChunk) / kFixChunk;
+  const int64_t gap0 = (int64_t)sr.prev_row + 1, ngap = ((int64_t)sr.row - gap0) * R;
+  for (int64_t i = threadIdx.x; i < ngap; i += blockDim.x) out[gap0 * R + i] = 0.f;
+  if (sr.is_last) {
+    const int64_t t0 = (int64_t)sr.row + 1, nt = (out_rows - t0) * R;
+    for (int64_t i = threadIdx.x; i < nt; i += blockDim.x) out[t0 * R + i] = 0.f;
+  }
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    float acc = 0.f;
+    for (int q = 0; q < nc; ++q) acc += chunk_sums[(size_t)(sr.chunk0 + q) * R + r];
     out[(int64_t)sr.row * R + r] = acc * sc;
   }
 }
 
-int launch_fixup(const float* part, const SplitRow* splits, int nsplit, float* out,
-                 int64_t out_rows, int R, const float* scale, cudaStream_t s) {
+int launch_fixup(const float* part, const SplitRow* splits, int nsplit, int nchunk,
+                 float* chunk_sums, float* out, int64_t out_rows, int R, const float* scale,
+                 cudaStream_t s) {
   if (nsplit <= 0) return SPM_OK;
-  splitrow_fixup_kernel<<<nsplit, 256, 0, s>>>(part, splits, nsplit, out, out_rows, R, scale);
+  splitrow_chunk_kernel<<<nchunk, 256, 0, s>>>(part, splits, nsplit, nchunk, R, chunk_sums);
+  splitrow_fixup_kernel<<<nsplit, 256, 0, s>>>(chunk_sums, splits, nsplit, out, out_rows, R,
+                                               scale);
   cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "splitrow_fixup_kernel launch");
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "split-row fix-up launch");
 }
 
 __global__ void zero_kernel(float4* __restrict__ out4, float* __restrict__ out, int64_t n4,

@@ -70,7 +70,7 @@ __global__ void na_splits_kernel(const uint8_t* __restrict__ elems, int es, int6
   sr.first_slot = 0;
   sr.prev_row = -1;
   sr.is_last = 0;  // rows after the last nonempty row are zeroed by na_tail_kernel
-  sr.pad0 = sr.pad1 = 0;
+  sr.chunk0 = sr.pad1 = 0;
   const int4 bi = blkinfo[b];
   const int64_t lo = bi.x, hi = bi.y;
   if (lo < hi && (bi.w & BLK_TAIL_SPLIT)) {

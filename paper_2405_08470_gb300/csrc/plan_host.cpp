@@ -247,7 +247,9 @@ int partition_mode(const spmttkrp_plan* p, int n, int nblk, ModeHost* out) {
       sr.first_slot = (m.bounds[sr.first_blk] == s) ? 0 : 1;
       sr.prev_row = u > 0 ? (int)ur[u - 1] : -1;
       sr.is_last = (e == nnz) ? 1 : 0;
-      sr.pad0 = sr.pad1 = 0;
+      sr.chunk0 = m.nchunk;
+      sr.pad1 = 0;
+      m.nchunk += (sr.last_blk - sr.first_blk + kFixChunk) / kFixChunk;
       m.splits.push_back(sr);
       last_u = u;
     }
