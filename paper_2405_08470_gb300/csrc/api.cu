@@ -189,8 +189,18 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   return launch_zero_listed_rows(out, d.empty_rows, d.nempty, p->R, p->stream);
 }
 
+const char* nvtx_mode_name(int n) {
+  static const char* names[] = {
+      "spmttkrp mode 0",  "spmttkrp mode 1",  "spmttkrp mode 2",  "spmttkrp mode 3",
+      "spmttkrp mode 4",  "spmttkrp mode 5",  "spmttkrp mode 6",  "spmttkrp mode 7",
+      "spmttkrp mode 8",  "spmttkrp mode 9",  "spmttkrp mode 10", "spmttkrp mode 11",
+      "spmttkrp mode 12", "spmttkrp mode 13", "spmttkrp mode 14", "spmttkrp mode 15"};
+  return (n >= 0 && n < 16) ? names[n] : "spmttkrp mode";
+}
+
 int compute_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
                  bool keep_order) {
+  NvtxRange range(nvtx_mode_name(mode));
   while (p->cur_mode != mode) {
     int st = remap_step(p);
     if (st) return st;
@@ -239,6 +249,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
                          const spmttkrp_opts_t* opts) {
   if (!out) return fail(SPM_ERR_INVALID_ARG, "out is null");
   *out = nullptr;
+  NvtxRange range("spmttkrp plan build");
   if (nmodes < 2) return fail(SPM_ERR_INVALID_ARG, "nmodes must be >= 2");
   if (nmodes > kMaxModes) return fail(SPM_ERR_UNSUPPORTED, "nmodes > 16");
   if (rank < 1) return fail(SPM_ERR_INVALID_ARG, "rank must be >= 1");
@@ -365,6 +376,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
       }
     }
     if (!st && device_orders) {
+      NvtxRange orders("spmttkrp plan orders on the device");
       std::vector<int32_t*> np((size_t)N);
       for (int n = 0; n < N; ++n) np[(size_t)n] = p->md[(size_t)n].next_pos;
       try {
@@ -464,6 +476,7 @@ int spmttkrp_compute(spmttkrp_plan_t p, int mode, const void* const* factors, fl
 
 int spmttkrp_sweep(spmttkrp_plan_t p, const void* const* factors, float* const* outs,
                    int flags) {
+  NvtxRange range("spmttkrp sweep");
   int st = check_plan(p);
   if (st) return st;
   st = check_factors(p, factors, -1);

@@ -164,6 +164,7 @@ using namespace spm;
 extern "C" {
 
 int cp_als_iter(spmttkrp_plan_t p, void* const* factors, float* lambda, double* fit) {
+  NvtxRange range("cp_als_iter");
   if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
   if (p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
   if (!factors || !lambda || !fit) return fail(SPM_ERR_INVALID_ARG, "null argument");
@@ -231,6 +232,7 @@ int cp_als_iter(spmttkrp_plan_t p, void* const* factors, float* lambda, double* 
 }
 
 int cp_loss_fwd(spmttkrp_plan_t p, const void* const* factors, float* loss) {
+  NvtxRange range("cp_loss_fwd");
   if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
   if (p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
   if (!factors || !loss) return fail(SPM_ERR_INVALID_ARG, "null argument");
@@ -251,6 +253,7 @@ int cp_loss_fwd(spmttkrp_plan_t p, const void* const* factors, float* loss) {
 
 int cp_loss_bwd(spmttkrp_plan_t p, const void* const* factors, const float* grad_out,
                 float* const* grads) {
+  NvtxRange range("cp_loss_bwd");
   if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
   if (p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
   if (!factors || !grad_out || !grads) return fail(SPM_ERR_INVALID_ARG, "null argument");
@@ -276,6 +279,7 @@ int cp_loss_bwd(spmttkrp_plan_t p, const void* const* factors, const float* grad
 
 int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* const* scratch,
                       int flags) {
+  NvtxRange range("spmttkrp autotune");
   if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
   if (p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
   if (!factors || !scratch) return fail(SPM_ERR_INVALID_ARG, "null argument");

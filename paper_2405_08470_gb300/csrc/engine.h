@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/spmttkrp.h"
 
 namespace spm {
@@ -127,6 +129,17 @@ struct spmttkrp_plan {
 };
 
 namespace spm {
+
+// Named NVTX range over a host-side scope (plan build, a mode's pass, a sweep,
+// an ALS iteration ...), so a profiler timeline shows the engine's phases.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+// "spmttkrp mode <n>" for n < kMaxModes
+const char* nvtx_mode_name(int n);
 
 // ---- error reporting (thread-local last error) ----
 int fail(int status, const std::string& msg);

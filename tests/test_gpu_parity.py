@@ -246,3 +246,24 @@ def test_compute_keep_order(keep_base):
     torch.cuda.synchronize()
     assert torch.equal(out, ref[2]) and p.info()["cur_mode"] == 0
     p.close()
+
+
+def test_device_memory_cap_is_a_status():
+    # fault injection through the allocation cap: plan creation fails cleanly with
+    # SPM_ERR_OOM, and a plan within the cap works afterwards
+    from paper_2405_08470_gb300 import SpmError
+    dims = (300, 200, 100)
+    coo, vals = synth.make_coo(dims, 50_000, (1.1, 1.1, 0.0), seed=6)
+    c, v = coo.numpy(), vals.numpy()
+    with pytest.raises(SpmError) as ei:
+        Plan(c, v, dims, 16, max_bytes=1 << 20)   # the two 1.6 MB copies alone exceed it
+    assert ei.value.status == -4
+    p = Plan(c, v, dims, 16, max_bytes=1 << 30)
+    assert 0 < p.info()["device_bytes"] <= 1 << 30
+    F = [f.cuda() for f in synth.make_factors(dims, 16, seed=7)]
+    out = torch.empty(dims[0], 16, device="cuda")
+    p.compute(0, F, out)
+    torch.cuda.synchronize()
+    assert O.relerr(out.cpu().numpy().astype(np.float64),
+                    O.mttkrp(c, v, dims, [f.cpu().numpy() for f in F], 0)) <= 1e-5
+    p.close()
