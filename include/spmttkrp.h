@@ -289,6 +289,35 @@ int spmttkrp_compute_noalloc(const void* elems, int64_t nnz, int nmodes, int mod
  * (e.g. SPM_ERR_TIMEOUT) and clears it. */
 int spmttkrp_device_status(spmttkrp_plan_t plan);
 
+/* Consistency check of a working copy on the device (Section 3.5: one pass's
+ * remap scatters every nonzero to exactly one place of the next order).  It
+ * reads only; nothing traps.  Checks, in this order of reported status:
+ *   - every index of every nonzero lies in [0, dims[k])     -> SPM_ERR_INDEX_RANGE
+ *   - next_pos (if given) holds ids in [0, nnz), each hit
+ *     exactly once (a permutation)                           -> SPM_ERR_STATE
+ *   - word alpha_word of every nonzero (if > 0) equals its
+ *     next_pos entry (remap ids carried in the padding)      -> SPM_ERR_STATE
+ * The last-error text gives the count of violations and the first position.
+ *   elems       device, nnz nonzeros of elem_bytes each: int32 idx[nmodes],
+ *               float value, then padding (elem_bytes a multiple of 16).
+ *   dims        host, int64 [nmodes].
+ *   next_pos    device int32 [nnz] or NULL (no remap checks).
+ *   alpha_word  0, or the 32-bit word index (> nmodes, inside elem_bytes) of
+ *               the remap id carried in each nonzero.
+ *   stream      cudaStream_t (NULL = default); the call synchronizes it.
+ * Allocates nnz * 4 bytes of device scratch for the hit counters (freed before
+ * return; not counted against a plan's max_bytes).  Errors: INVALID_ARG, CUDA,
+ * and the statuses above. */
+int spmttkrp_check_elements(const void* elems, int64_t nnz, int nmodes, const int64_t* dims,
+                            int elem_bytes, const int32_t* next_pos, int alpha_word,
+                            void* stream);
+
+/* The same check on a plan's own working copy in its current mode's order,
+ * with that mode's next_pos and, for plans that carry remap ids in their
+ * nonzeros, the id word of the next mode.  Errors: INVALID_ARG, STATE
+ * (host-only plan, or a failed check), INDEX_RANGE, CUDA. */
+int spmttkrp_plan_check(spmttkrp_plan_t plan);
+
 /* Thread-local text for the last non-OK status of this thread. */
 const char* spmttkrp_last_error(void);
 

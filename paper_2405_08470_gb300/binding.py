@@ -87,6 +87,9 @@ def lib():
     L.spmttkrp_autotune.argtypes = [P, P, P, ctypes.c_int]
     L.spmttkrp_plan_query.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t]
     L.spmttkrp_device_status.argtypes = [P]
+    L.spmttkrp_check_elements.argtypes = [P, ctypes.c_int64, ctypes.c_int, I64P, ctypes.c_int,
+                                          P, ctypes.c_int, P]
+    L.spmttkrp_plan_check.argtypes = [P]
     for name in declared_functions():
         getattr(L, name).restype = ctypes.c_char_p if name == "spmttkrp_last_error" \
             else ctypes.c_int
@@ -114,6 +117,20 @@ def _stream_ptr(stream):
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream) if hasattr(stream, "cuda_stream") \
         else ctypes.c_void_p(stream)
+
+
+def check_elements(elems, nnz: int, dims, elem_bytes: int, next_pos=None, alpha_word: int = 0,
+                   stream=None):
+    """Device check of a working copy held in a CUDA tensor `elems` (nnz records of
+    elem_bytes: int32 indices, float value, padding).  `next_pos` is an int32 CUDA tensor
+    or None; `alpha_word` the word index of a carried remap id (0 = none).  Raises
+    SpmError (INDEX_RANGE or STATE) on a violation."""
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int64))
+    check(lib().spmttkrp_check_elements(
+        ctypes.c_void_p(elems.data_ptr()), int(nnz), len(d),
+        d.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(elem_bytes),
+        None if next_pos is None else ctypes.c_void_p(next_pos.data_ptr()), int(alpha_word),
+        _stream_ptr(stream)))
 
 
 class Plan:
@@ -208,6 +225,11 @@ class Plan:
 
     def device_status(self):
         check(lib().spmttkrp_device_status(self._h))
+
+    def check(self):
+        """Device check of the working copy: indices in range, next_pos a permutation,
+        carried remap ids equal to next_pos.  Raises SpmError on a violation."""
+        check(lib().spmttkrp_plan_check(self._h))
 
     # -- queries
     def info(self, mode: int = 0) -> dict:
