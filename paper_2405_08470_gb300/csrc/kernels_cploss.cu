@@ -84,14 +84,22 @@ __global__ void __launch_bounds__(256) cp_fwd_kernel(const uint8_t* __restrict__
   }
 }
 
+// Starts a bulk copy of `bytes` (a multiple of 16, 16-byte aligned source) into
+// L2 without waiting for it; nothing lands in shared memory or registers.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Batched form for 3 and 4 modes on the 16-byte-slice path: each lane group takes
 // U consecutive nonzeros at a time, issues all their factor-row slice loads before
 // using any (U * N 16-byte loads in flight per lane), reduces the U model values
 // with interleaved shuffles, and writes the U residual nonzeros with one 16-byte
 // chunk per lane.  Same products and sums per nonzero as cp_fwd_kernel; the loss is
-// accumulated per lane in a fixed order.
+// accumulated per lane in a fixed order.  The warp's nonzeros of the next
+// iteration are prefetched into L2 while this one waits on its factor rows, so
+// only the gather latency stays on the loop's critical path.
 template <int NT, typename T, int VW, int U>
-__global__ void __launch_bounds__(256) cp_fwd_batched_kernel(const uint8_t* __restrict__ elems,
+__global__ void __launch_bounds__(256, 4) cp_fwd_batched_kernel(const uint8_t* __restrict__ elems,
                                                              uint8_t* __restrict__ res,
                                                              int64_t nnz, int es, FactorPtrs fp,
                                                              int R, int L,
@@ -104,7 +112,12 @@ __global__ void __launch_bounds__(256) cp_fwd_batched_kernel(const uint8_t* __re
   const int nv = es / 16;
   const uint64_t pol = make_policy(2);  // factor rows are reused: evict last in L2
   double sq = 0.0;
-  for (int64_t base = wid * per_warp; base < nnz; base += nw * per_warp) {  // warp-uniform
+  const int64_t stride = nw * per_warp;
+  for (int64_t base = wid * per_warp; base < nnz; base += stride) {  // warp-uniform
+    if (lane == 0 && base + stride < nnz) {
+      const int64_t next = base + stride, cnt = min(per_warp, nnz - next);
+      prefetch_l2_bulk(elems + next * es, (uint32_t)(cnt * es));
+    }
     int idx[U][NT];
     float val[U];
     bool act[U];
@@ -196,22 +209,39 @@ __global__ void cp_loss_final_kernel(const double* __restrict__ part, int nb,
   loss[0] = (float)(0.5 * s);
 }
 
+// Grid of the forward: the CTAs that are resident at once (a multiple of the SM
+// count), capped by the partial-sum slots; every CTA strides over the whole copy.
+template <typename K>
+static int resident_grid(K kernel, int cap) {
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0) != cudaSuccess ||
+      occ < 1)
+    return cap;
+  return std::max(1, std::min(cap, occ * sms));
+}
+
 template <typename T>
 static int fwd_dispatch(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N,
-                        const FactorPtrs& fp, int R, bool aligned, double* part, int nb,
+                        const FactorPtrs& fp, int R, bool aligned, double* part, int cap,
                         cudaStream_t s) {
   const int dtype = std::is_same<T, float>::value ? SPM_DTYPE_F32 : SPM_DTYPE_BF16;
   const LaneCfg c = lane_config(R, dtype, aligned);
   constexpr int VWV = std::is_same<T, float>::value ? 4 : 8;
+  int nb = cap;
   if (c.vec) {
-    if (N == 3)
+    if (N == 3) {
+      nb = resident_grid(cp_fwd_batched_kernel<3, T, VWV, 4>, cap);
       cp_fwd_batched_kernel<3, T, VWV, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, fp, R, c.L,
                                                              part);
-    else if (N == 4)
+    } else if (N == 4) {
+      nb = resident_grid(cp_fwd_batched_kernel<4, T, VWV, 4>, cap);
       cp_fwd_batched_kernel<4, T, VWV, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, fp, R, c.L,
                                                              part);
-    else
+    } else {
       cp_fwd_kernel<0, T, VWV, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part);
+    }
   } else {
     switch (c.RC) {
       case 1: cp_fwd_kernel<0, T, 1, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part); break;
@@ -220,7 +250,7 @@ static int fwd_dispatch(const uint8_t* elems, uint8_t* res, int64_t nnz, int es,
       default: cp_fwd_kernel<0, T, 1, 8><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part); break;
     }
   }
-  return SPM_OK;
+  return nb;
 }
 
 int launch_cp_fwd(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N,
@@ -228,11 +258,11 @@ int launch_cp_fwd(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N
                   double* loss64, cudaStream_t s) {
   bool aligned = true;
   for (int k = 0; k < N; ++k) aligned = aligned && (((uintptr_t)fp.p[k] & 15u) == 0);
-  if (dtype == SPM_DTYPE_BF16)
-    fwd_dispatch<__nv_bfloat16>(elems, res, nnz, es, N, fp, R, aligned, part, nb, s);
-  else
-    fwd_dispatch<float>(elems, res, nnz, es, N, fp, R, aligned, part, nb, s);
-  cp_loss_final_kernel<<<1, 32, 0, s>>>(part, nb, loss, loss64);
+  const int used = dtype == SPM_DTYPE_BF16
+                       ? fwd_dispatch<__nv_bfloat16>(elems, res, nnz, es, N, fp, R, aligned, part,
+                                                     nb, s)
+                       : fwd_dispatch<float>(elems, res, nnz, es, N, fp, R, aligned, part, nb, s);
+  cp_loss_final_kernel<<<1, 32, 0, s>>>(part, used, loss, loss64);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SPM_OK : cuda_fail(e, "cp_fwd kernels");
 }
