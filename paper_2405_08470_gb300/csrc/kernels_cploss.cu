@@ -23,6 +23,8 @@ __global__ void __launch_bounds__(256) cp_fwd_kernel(const uint8_t* __restrict__
   const int64_t gid = ((int64_t)blockIdx.x * 8 + w) * G + gw;
   const int64_t ngroups = (int64_t)gridDim.x * 8 * G;
   double sq = 0.0;
+  float run = 0.f;  // FP32 sum of up to 8 squared residuals, then added to sq
+  int nrun = 0;
   // the loop bound is uniform across the warp so that the shuffles below see
   // every lane; groups past the end carry an inactive flag
   for (int64_t eb = gid - gw; eb < nnz; eb += ngroups) {
@@ -59,7 +61,7 @@ __global__ void __launch_bounds__(256) cp_fwd_kernel(const uint8_t* __restrict__
     if (active && sub == 0) {
       const float x = __int_as_float(__ldg(el + N));
       const float r = m - x;
-      sq += (double)r * (double)r;
+      run = fmaf(r, r, run);
       const int nv = es / 16;
       const uint4* src = reinterpret_cast<const uint4*>(el);
       uint4* dst = reinterpret_cast<uint4*>(res + e * es);
@@ -73,7 +75,13 @@ __global__ void __launch_bounds__(256) cp_fwd_kernel(const uint8_t* __restrict__
         dst[c] = v;
       }
     }
+    if (++nrun == 8) {  // warp-uniform count of iterations
+      sq += (double)run;
+      run = 0.f;
+      nrun = 0;
+    }
   }
+  sq += (double)run;
   __shared__ double red[256];
   red[threadIdx.x] = sq;
   __syncthreads();
@@ -162,12 +170,16 @@ __global__ void __launch_bounds__(256, 4) cp_fwd_batched_kernel(const uint8_t* _
     for (int off = L / 2; off > 0; off >>= 1)
 #pragma unroll
       for (int u = 0; u < U; ++u) m[u] += __shfl_xor_sync(0xffffffffu, m[u], off);
-    float r[U];
+    // the U squared residuals are summed in FP32 and added to the FP64 total once
+    // per iteration: FP64 issues slowly on this part, once per nonzero it bounds
+    // the loop
+    float r[U], s4 = 0.f;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       r[u] = m[u] - val[u];
-      if (act[u] && sub == 0) sq += (double)r[u] * (double)r[u];
+      if (act[u]) s4 = fmaf(r[u], r[u], s4);
     }
+    if (sub == 0) sq += (double)s4;
     // residual copy: chunk c of nonzero u per lane, the value word replaced by e_e
     for (int j = sub; j < U * nv; j += L) {
       const int u = j / nv, c = j - u * nv;
