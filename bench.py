@@ -193,9 +193,10 @@ def kernel_digest():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload, R, dtype):
+def ncu_traffic(workload, R, dtype, nnz, info):
     """DRAM bytes per launch of the fused kernel from a committed ncu summary, if its
-    kernel digest matches the current sources (else null: counters are stale)."""
+    kernel digest matches the current sources and the run has the captured
+    configuration (size, blocks, tile, ring depth, stride, plan options); else null."""
     path = os.path.join(PROFILES, "mttkrp_remap_traffic.json")
     if not os.path.exists(path):
         return None
@@ -207,7 +208,12 @@ def ncu_traffic(workload, R, dtype):
         return None
     key = f"{workload}_R{R}_{dtype}"
     e = d.get("entries", {}).get(key)
-    return e.get("dram_bytes_per_launch_full") if e else None
+    if not e:
+        return None
+    cfg = e.get("config", {})
+    if cfg.get("nnz") != nnz or any(info.get(k) != v for k, v in cfg.items() if k != "nnz"):
+        return None
+    return e.get("dram_bytes_per_launch_full")
 
 
 def cpu_oracle_sample(coo_h, vals_h, dims, R, target_s, seed):
@@ -543,7 +549,8 @@ def main():
     byts = compulsory_bytes(spec.dims, nnz, R, s, touched, N, args.keep_base)
     t_roof_ms = sum(byts) / (peak * 1e9) * 1e3
     achieved = sum(byts) / (per_mode.sum() * 1e-3) / 1e9
-    traffic = ncu_traffic(args.workload, R, args.dtype)
+    traffic = ncu_traffic(args.workload, R, args.dtype, nnz,
+                          dict(info, unroll=args.unroll or 8, cache_hints=args.hints))
     # per-nonzero gathers counted every time (no reuse in L1/L2), for comparison
     E = 4 * N + 4
     no_reuse = sum(nnz * (E + 4 + E) + nnz * (N - 1) * R * s + spec.dims[n] * R * 4
@@ -602,7 +609,9 @@ def main():
             "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": spec.name, "dims": list(spec.dims), "nnz": nnz, "rank": R,
+            "config": {"workload": spec.name if nnz == spec.nnz else
+                       f"{spec.name}; reduced to {nnz} nonzeros",
+                       "dims": list(spec.dims), "nnz": nnz, "rank": R,
                        "factor_dtype": args.dtype, "nblk": info["nblk"], "tile": info["tile"],
                        "kernel_form": ["warp blocks, bulk-async staged tiles",
                                        "CTA blocks, direct runs"][info["variant"]],
