@@ -23,7 +23,9 @@ def test_library_exports_every_declared_symbol():
                  "spmttkrp_compute", "spmttkrp_sweep", "cp_als_iter", "cp_loss_fwd",
                  "cp_loss_bwd", "spmttkrp_autotune", "spmttkrp_plan_query",
                  "spmttkrp_last_error", "spmttkrp_opts_init", "spmttkrp_set_stream",
-                 "spmttkrp_device_status", "spmttkrp_version"]:
+                 "spmttkrp_device_status", "spmttkrp_version", "spmttkrp_compute_ex",
+                 "spmttkrp_compute_noalloc", "spmttkrp_check_elements",
+                 "spmttkrp_plan_check"]:
         assert must in names
     for n in names:
         assert hasattr(L, n), n
@@ -155,4 +157,24 @@ def test_null_pointer_and_state_errors():
     # compute on a host-only plan is a state error, not a crash
     assert L.spmttkrp_compute(p._h, 0, None, None) == -8
     assert L.spmttkrp_remap(p._h, 5) == -8
+    p.close()
+
+
+def test_check_argument_errors_need_no_device():
+    """The consistency check rejects bad arguments before touching the device, and
+    refuses host-only plans."""
+    L = lib()
+    dims_np = np.array([4, 4, 4], dtype=np.int64)
+    dims = dims_np.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    cases = [(-1, 3, 32, 0), (8, 1, 32, 0), (8, 3, 24, 0), (8, 3, 12, 0), (8, 3, 32, 3),
+             (8, 3, 32, 8)]
+    buf = ctypes.c_void_p(1)  # never dereferenced: every case fails its argument checks
+    for nnz, N, eb, aw in cases:
+        assert L.spmttkrp_check_elements(buf, nnz, N, dims, eb, None, aw, None) == -1, \
+            (nnz, N, eb, aw)
+    coo, vals = synth.make_coo((20, 10, 5), 200, (0.0, 0.0, 0.0), seed=2)
+    p = _host_plan(coo.numpy(), vals.numpy(), (20, 10, 5))
+    with pytest.raises(SpmError) as ei:
+        p.check()
+    assert ei.value.status == -8
     p.close()
