@@ -5,7 +5,9 @@
 // the spMTTKRP kernel), the model value is summed across the group with
 // shuffles, and the nonzero is written to the residual copy with its value
 // replaced by e_e.  The gradient is then one all-mode spMTTKRP sweep of the
-// residual copy.  The loss is reduced in a fixed order (FP64).
+// residual copy.  The loss is reduced in a fixed order: each lane adds short
+// runs of squared residuals in FP32 to its FP64 total, then the lanes, CTAs and
+// partial sums are added in FP64 in index order.
 #include "als.h"
 #include "mttkrp_kernel.cuh"
 
