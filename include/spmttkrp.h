@@ -76,7 +76,12 @@ typedef struct {
                        only spmttkrp_plan_query and destroy are then valid        */
   int variant;      /* fused kernel form: 0 = one warp per block, tiles staged in
                        shared memory by bulk async copies (default); 1 = one CTA
-                       per block, each lane group streams one contiguous run     */
+                       per block, each lane group streams one contiguous run;
+                       2 = tile form (3 modes, 32-byte nonzeros, R = 16, 32 or 64,
+                       16-byte aligned factors and outputs; otherwise form 0 runs):
+                       persistent CTAs stage tiles of 960 consecutive nonzeros,
+                       issue the remap stores in destination order, and keep
+                       several gathers in flight per lane group                 */
   int unroll;       /* nonzeros in flight per lane group in form 0: 0 (= 8), 4, 8 */
   int stages;       /* tiles per warp ring in form 0: 0 (= 2 for 32-byte and wider
                        nonzeros, 3 for 16-byte ones), 2, 3 or 4                   */
@@ -105,6 +110,17 @@ typedef struct {
                        max_bytes); 1 = on the host (parallel C++ radix passes).
                        Both give the same plan bit for bit.  Host-only plans and
                        partition 1 always build on the host.                    */
+  int64_t wait_limit_ns; /* limit of the fused kernels' bounded waits on their
+                       bulk-copy barriers before they give up and record
+                       SPM_ERR_TIMEOUT (read by spmttkrp_device_status);
+                       0 = 2 s.  Copies already in flight are still awaited
+                       (with the 2 s limit) before a giving-up warp returns.    */
+  int inject_wait_stall; /* failure-injection test switch: 1 = the first wait of
+                       every warp of the fused kernel is on a barrier that nothing
+                       completes, so it runs out after wait_limit_ns and the
+                       pass reports SPM_ERR_TIMEOUT without writing its outputs;
+                       the device context stays usable.  0 = off (always, except
+                       in tests of the give-up path).                          */
 } spmttkrp_opts_t;
 
 /* Fills *opts with the defaults (FP32, contiguous split, automatic sizes). */
@@ -247,7 +263,12 @@ enum {
   SPM_Q_SPLITS = 3,   /* int64[nsplit][3]: (row, first_blk, last_blk) of `mode`   */
   SPM_Q_ELEMS = 4,    /* int32[nnz][nmodes] indices of the working copy, in its
                          current order                                             */
-  SPM_Q_VALS = 5      /* float[nnz] values of the working copy, same order         */
+  SPM_Q_VALS = 5,     /* float[nnz] values of the working copy, same order         */
+  SPM_Q_RAW = 6       /* uint8[nnz][elem_bytes]: the stored nonzeros of the working
+                         copy in its current order, padding words included (for a
+                         3-mode plan in 32-byte sectors: words 4..6 = the nonzero's
+                         positions in the three orders, word 7 = the write orders
+                         of the tile form, 10 bits per mode)                       */
 };
 
 /* Copies plan data into host memory (synchronizes).  bytes must be >= the

@@ -325,6 +325,21 @@ def lpt_remap_ids(coo, n, kappa):
     return rid
 
 
+def tile_write_order(coo, n, tile):
+    """Write order of one mode pass cut into tiles of `tile` consecutive
+    positions of the mode-n order: for each tile, its tile-local indices sorted
+    by destination in the mode-(n+1) order (next_pos, Section 3.1).  Storing a
+    tile's nonzeros in this order visits their destinations in increasing
+    order; the remap itself (where each nonzero goes) is unchanged.
+    Returns int64 [nnz]: entry base + j is the local index written j-th."""
+    npos = next_pos(coo, n)
+    out = np.empty_like(npos)
+    for base in range(0, npos.shape[0], int(tile)):
+        seg = npos[base:base + int(tile)]
+        out[base:base + seg.shape[0]] = np.argsort(seg, kind="stable")
+    return out
+
+
 def flycoo_bits(nnz, dims, value_bits=32):
     """Bits per nonzero of the FLYCOO element (Section 3.5.1).
 

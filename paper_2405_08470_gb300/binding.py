@@ -24,7 +24,7 @@ STATUS = {
     -8: "SPM_ERR_STATE", -9: "SPM_ERR_TIMEOUT",
 }
 DTYPES = {"f32": 0, "bf16": 1}
-Q_INFO, Q_NEXT_POS, Q_BOUNDS, Q_SPLITS, Q_ELEMS, Q_VALS = range(6)
+Q_INFO, Q_NEXT_POS, Q_BOUNDS, Q_SPLITS, Q_ELEMS, Q_VALS, Q_RAW = range(7)
 SWEEP_GRAPH = 1
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
@@ -47,7 +47,9 @@ class Opts(ctypes.Structure):
                 ("cache_hints", ctypes.c_int),
                 ("stream", ctypes.c_void_p),
                 ("keep_base", ctypes.c_int),
-                ("plan_on_host", ctypes.c_int)]
+                ("plan_on_host", ctypes.c_int),
+                ("wait_limit_ns", ctypes.c_int64),
+                ("inject_wait_stall", ctypes.c_int)]
 
 
 _LIB = None
@@ -140,7 +142,8 @@ class Plan:
                  nblk: int = 0, tile: int = 0, max_bytes: int = 0, checks: bool = False,
                  host_only: bool = False, stream=None, variant: int = 0, unroll: int = 0,
                  cache_hints: int = 0, stages: int = 0, element_bytes: int = 0,
-                 keep_base: bool = False, partition: int = 0, plan_on_host: bool = False):
+                 keep_base: bool = False, partition: int = 0, plan_on_host: bool = False,
+                 wait_limit_ns: int = 0, inject_wait_stall: bool = False):
         L = lib()
         coo = np.ascontiguousarray(np.asarray(coo.cpu() if hasattr(coo, "cpu") else coo,
                                               dtype=np.int64))
@@ -162,7 +165,13 @@ class Plan:
         o.keep_base = int(bool(keep_base))
         o.partition = int(partition)
         o.plan_on_host = int(bool(plan_on_host))
+        o.wait_limit_ns = int(wait_limit_ns)
+        o.inject_wait_stall = int(bool(inject_wait_stall))
+        # without an explicit stream the plan follows torch's current stream at
+        # every call (so its work is ordered with the caller's tensors)
+        self._follow = stream is None and not host_only
         o.stream = None if host_only else _stream_ptr(stream)
+        self._stream = None if host_only else o.stream
         d = np.asarray(self.dims, dtype=np.int64)
         h = ctypes.c_void_p()
         st = L.spmttkrp_plan_create(ctypes.byref(h),
@@ -172,6 +181,12 @@ class Plan:
                                     ctypes.byref(o))
         check(st)
         self._h = h
+        self._device = None
+        if not host_only:
+            import torch
+            if torch.cuda.is_available():
+                self._device = torch.cuda.current_device()
+        self.loss_generation = 0  # bumped by every cp_loss_fwd / cp_loss_bwd
 
     # -- lifetime
     def close(self):
@@ -186,15 +201,60 @@ class Plan:
             pass
 
     def set_stream(self, stream):
-        check(lib().spmttkrp_set_stream(self._h, _stream_ptr(stream)))
+        self._follow = False
+        self._stream = _stream_ptr(stream)
+        check(lib().spmttkrp_set_stream(self._h, self._stream))
+
+    # -- argument checks (before any pointer reaches the C ABI)
+    def _sync_stream(self):
+        if not self._follow:
+            return
+        import torch
+        cur = torch.cuda.current_stream().cuda_stream
+        if self._stream is None or self._stream.value != cur:
+            self._stream = ctypes.c_void_p(cur)
+            check(lib().spmttkrp_set_stream(self._h, self._stream))
+
+    def _check_tensor(self, t, rows, what, dtype=None):
+        import torch
+        want = dtype or (torch.bfloat16 if self.dtype == "bf16" else torch.float32)
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{what}: expected a torch.Tensor")
+        if not t.is_cuda or (self._device is not None and t.device.index != self._device):
+            raise ValueError(f"{what}: must be on the plan's CUDA device")
+        if t.dtype != want:
+            raise ValueError(f"{what}: dtype {t.dtype}, the plan needs {want}")
+        if tuple(t.shape) != (rows, self.rank):
+            raise ValueError(f"{what}: shape {tuple(t.shape)}, expected {(rows, self.rank)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{what}: must be contiguous (row-major I x R)")
+
+    def _check_factors(self, factors, skip=-1):
+        if len(factors) != self.nmodes:
+            raise ValueError(f"expected {self.nmodes} factors, got {len(factors)}")
+        for k, f in enumerate(factors):
+            if k != skip:
+                self._check_tensor(f, self.dims[k], f"factor {k}")
+
+    def _check_outs(self, outs, what="output"):
+        import torch
+        if len(outs) != self.nmodes:
+            raise ValueError(f"expected {self.nmodes} {what}s, got {len(outs)}")
+        for k, o in enumerate(outs):
+            self._check_tensor(o, self.dims[k], f"{what} {k}", torch.float32)
 
     # -- compute
     def remap(self, mode: int):
+        self._sync_stream()
         check(lib().spmttkrp_remap(self._h, int(mode)))
 
     def compute(self, mode: int, factors, out, keep_order: bool = False):
         """Mode-n spMTTKRP into out; with keep_order the pass writes no remap and the
         working copy stays in mode-n order."""
+        import torch
+        self._check_factors(factors, skip=int(mode))
+        self._check_tensor(out, self.dims[int(mode)], "out", torch.float32)
+        self._sync_stream()
         if keep_order:
             check(lib().spmttkrp_compute_ex(self._h, int(mode), _ptrs(factors),
                                             ctypes.c_void_p(out.data_ptr()), 1))
@@ -203,23 +263,54 @@ class Plan:
                                      ctypes.c_void_p(out.data_ptr())))
 
     def sweep(self, factors, outs, graph: bool = False):
+        self._check_factors(factors)
+        self._check_outs(outs)
+        self._sync_stream()
         check(lib().spmttkrp_sweep(self._h, _ptrs(factors), _ptrs(outs),
                                    SWEEP_GRAPH if graph else 0))
 
     def als_iter(self, factors, lam) -> float:
+        import torch
+        self._check_factors(factors)
+        if lam.dtype != torch.float32 or lam.numel() != self.rank or not lam.is_contiguous():
+            raise ValueError("lambda: contiguous float32 tensor of rank elements")
+        self._sync_stream()
         fit = ctypes.c_double()
         check(lib().cp_als_iter(self._h, _ptrs(factors), ctypes.c_void_p(lam.data_ptr()),
                                 ctypes.byref(fit)))
         return fit.value
 
     def loss_fwd(self, factors, loss):
+        """CP-loss forward; its residuals stay in the plan for the next loss_bwd.
+        Returns the plan's loss generation, which this call advances."""
+        import torch
+        self._check_factors(factors)
+        if loss.dtype != torch.float32 or loss.numel() != 1:
+            raise ValueError("loss: float32 scalar tensor")
+        self._sync_stream()
         check(lib().cp_loss_fwd(self._h, _ptrs(factors), ctypes.c_void_p(loss.data_ptr())))
+        self.loss_generation += 1
+        return self.loss_generation
 
     def loss_bwd(self, factors, grad_out, grads):
-        check(lib().cp_loss_bwd(self._h, _ptrs(factors), ctypes.c_void_p(grad_out.data_ptr()),
-                                _ptrs(grads)))
+        """CP-loss gradients from the residuals of the last loss_fwd (which this
+        call consumes, advancing the loss generation)."""
+        import torch
+        self._check_factors(factors)
+        self._check_outs(grads, "gradient")
+        if grad_out.dtype != torch.float32 or grad_out.numel() != 1:
+            raise ValueError("grad_out: float32 scalar tensor")
+        self._sync_stream()
+        try:
+            check(lib().cp_loss_bwd(self._h, _ptrs(factors),
+                                    ctypes.c_void_p(grad_out.data_ptr()), _ptrs(grads)))
+        finally:
+            self.loss_generation += 1
 
     def autotune(self, factors, scratch, ignore_cache: bool = False):
+        self._check_factors(factors)
+        self._check_outs(scratch, "scratch")
+        self._sync_stream()
         check(lib().spmttkrp_autotune(self._h, _ptrs(factors), _ptrs(scratch),
                                       1 if ignore_cache else 0))
 
@@ -266,6 +357,14 @@ class Plan:
         check(lib().spmttkrp_plan_query(self._h, Q_SPLITS, int(mode),
                                         out.ctypes.data if ns else
                                         np.zeros(1, np.int64).ctypes.data, max(out.nbytes, 8)))
+        return out
+
+    def raw_elements(self) -> np.ndarray:
+        """Stored nonzeros of the working copy as int32 words [nnz, elem_bytes / 4]."""
+        es = self.info()["elem_bytes"]
+        out = np.zeros((self.nnz, es // 4), dtype=np.int32)
+        if self.nnz:
+            check(lib().spmttkrp_plan_query(self._h, Q_RAW, 0, out.ctypes.data, out.nbytes))
         return out
 
     def elements(self):

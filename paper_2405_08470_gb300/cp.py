@@ -17,11 +17,16 @@ from .binding import Plan
 
 
 class CPLoss(torch.autograd.Function):
+    """The plan holds the residuals of its latest forward only.  Each forward
+    records the plan's loss generation; a backward whose forward is no longer
+    the latest (another forward ran since, or an earlier backward consumed the
+    residuals) first recomputes its residuals from its saved factors."""
+
     @staticmethod
     def forward(ctx, plan: Plan, *factors):
         fs = [f.contiguous() for f in factors]
         loss = torch.empty((), device=fs[0].device, dtype=torch.float32)
-        plan.loss_fwd(fs, loss)
+        ctx.generation = plan.loss_fwd(fs, loss)
         ctx.plan = plan
         ctx.save_for_backward(*fs)
         return loss
@@ -29,6 +34,9 @@ class CPLoss(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         fs = ctx.saved_tensors
+        if ctx.plan.loss_generation != ctx.generation:
+            scratch = torch.empty((), device=fs[0].device, dtype=torch.float32)
+            ctx.plan.loss_fwd(fs, scratch)
         grads = [torch.empty(f.shape, device=f.device, dtype=torch.float32) for f in fs]
         g = grad_out.detach().to(torch.float32).contiguous().reshape(())
         ctx.plan.loss_bwd(fs, g, grads)

@@ -2,8 +2,11 @@
 // the all-mode sweep (Algorithm 5), plus plan queries and error reporting.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 
 #include "als.h"
 #include "engine.h"
@@ -21,6 +24,22 @@ int fail(int status, const std::string& msg) {
 int cuda_fail(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
   return SPM_ERR_CUDA;
+}
+
+int ensure_dyn_smem(const void* kernel, size_t bytes, const char* what) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> done;  // (kernel, device) -> limit set
+  int dev = 0;
+  SPM_CUDA(cudaGetDevice(&dev));
+  const size_t want = std::max<size_t>(bytes, 48 * 1024);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = done[std::make_pair(kernel, dev)];
+  if (have >= want) return SPM_OK;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)want);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  have = want;
+  return SPM_OK;
 }
 
 int plan_dalloc(spmttkrp_plan* p, void** ptr, size_t bytes) {
@@ -144,6 +163,9 @@ static int check_device_word(spmttkrp_plan* p) {
   SPM_CUDA(cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) {
     SPM_CUDA(cudaMemset(p->d_err, 0, sizeof(int)));
+    if (h & 2)
+      return fail(SPM_ERR_STATE,
+                  "a stored nonzero's write order or remap id was out of range (store skipped)");
     return fail(SPM_ERR_TIMEOUT, "a bounded device wait gave up (bulk copy did not complete)");
   }
   return SPM_OK;
@@ -179,6 +201,11 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   a.unroll = p->unroll;
   a.stages = p->stages;
   a.no_fill = p->partition == 1;
+  a.wait_ns = p->wait_ns;
+  a.stall_test = p->stall_test;
+  a.nnz = p->nnz;
+  a.grid_ctas = p->num_sms;
+  if (a.variant == 2 && !p->worders) a.variant = 0;  // no write orders: form 0
   // the pass's elements carry their remap ids: word 4 + (next mode)
   a.alpha_word = p->alpha ? 4 + (mode + 1) % p->N : 0;
   int st = launch_mttkrp(a, p->stream);
@@ -272,7 +299,8 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   if (o.tile != 0 && o.tile != 32 && o.tile != 64 && o.tile != 128 && o.tile != 256)
     return fail(SPM_ERR_INVALID_ARG, "tile must be 0, 32, 64, 128 or 256");
   if (o.nblk < 0) return fail(SPM_ERR_INVALID_ARG, "nblk must be >= 0");
-  if (o.variant < 0 || o.variant > 1) return fail(SPM_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (o.variant < 0 || o.variant > 2)
+    return fail(SPM_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
   if (o.unroll != 0 && o.unroll != 4 && o.unroll != 8)
     return fail(SPM_ERR_INVALID_ARG, "unroll must be 0, 4 or 8");
   if (o.stages != 0 && (o.stages < 2 || o.stages > 4))
@@ -281,6 +309,9 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     return fail(SPM_ERR_INVALID_ARG, "cache_hints must be in [-1, 3]");
   if (o.keep_base != 0 && o.keep_base != 1)
     return fail(SPM_ERR_INVALID_ARG, "keep_base must be 0 or 1");
+  if (o.wait_limit_ns < 0) return fail(SPM_ERR_INVALID_ARG, "wait_limit_ns must be >= 0");
+  if (o.inject_wait_stall != 0 && o.inject_wait_stall != 1)
+    return fail(SPM_ERR_INVALID_ARG, "inject_wait_stall must be 0 or 1");
 
   spmttkrp_plan* p = new (std::nothrow) spmttkrp_plan();
   if (!p) return fail(SPM_ERR_OOM, "host allocation failed");
@@ -295,6 +326,8 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   p->checks = o.checks;
   p->keep_base = o.keep_base;
   p->partition = o.partition;
+  p->wait_ns = (unsigned long long)o.wait_limit_ns;
+  p->stall_test = o.inject_wait_stall;
   p->host_only = o.host_only;
   p->max_bytes = o.max_bytes;
   p->stream = (cudaStream_t)o.stream;
@@ -388,6 +421,9 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
         st = fail(SPM_ERR_OOM, "host allocation failed while planning");
       }
     }
+    // the tile form's write orders (3 modes, nonzeros carrying remap ids)
+    if (!st && p->alpha)
+      st = build_write_orders(p, p->keep_base ? p->d_base : p->d_elem[0]);
     for (int n = 0; n < N && !st; ++n) st = upload_mode_tables(p, n);
     if (!st) {
       cudaError_t e = cudaStreamSynchronize(p->stream);
@@ -554,7 +590,8 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
   auto need = [&](size_t b) -> int {
     return bytes < b ? fail(SPM_ERR_INVALID_ARG, "destination too small") : SPM_OK;
   };
-  if (what != SPM_Q_INFO && what != SPM_Q_ELEMS && what != SPM_Q_VALS && (mode < 0 || mode >= N))
+  if (what != SPM_Q_INFO && what != SPM_Q_ELEMS && what != SPM_Q_VALS && what != SPM_Q_RAW &&
+      (mode < 0 || mode >= N))
     return fail(SPM_ERR_INVALID_ARG, "mode out of range");
   switch (what) {
     case SPM_Q_INFO: {
@@ -638,6 +675,18 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
         else
           std::memcpy(o + (size_t)q * 4, e + (size_t)N * 4, 4);
       }
+      return SPM_OK;
+    }
+    case SPM_Q_RAW: {
+      const size_t bytes = (size_t)nnz * p->es;
+      if ((st = need(bytes))) return st;
+      if (nnz == 0) return SPM_OK;
+      if (p->host_only) {
+        std::memcpy(dst, p->h_elems.data(), bytes);
+        return SPM_OK;
+      }
+      SPM_CUDA(cudaStreamSynchronize(p->stream));
+      SPM_CUDA(cudaMemcpy(dst, cur_elems(p), bytes, cudaMemcpyDeviceToHost));
       return SPM_OK;
     }
     default:

@@ -76,6 +76,8 @@ struct spmttkrp_plan {
   int hints = 3;    // L2 cache policy bits of the fused kernel (see MttkrpArgs)
   int unroll = 0;   // nonzeros in flight per lane group of the warp-block form
   int stages = 3;   // tiles per warp ring of the warp-block form
+  unsigned long long wait_ns = 0;  // first-wait limit of the fused kernels (0 = 2 s)
+  int stall_test = 0;              // test only: the fused kernels' first wait never completes
   int64_t nnz = 0;
   int es = 16;  // element stride in bytes: {int32 idx[N]; float val}, rounded up to 16
   std::vector<int64_t> dims;
@@ -103,6 +105,7 @@ struct spmttkrp_plan {
   int partition = 0;             // 0 = contiguous split, 1 = Algorithm 1 (LPT)
   int alpha = 0;  // stored nonzeros carry their remap ids: words 4..6 = position in
                   // the mode-0/1/2 order (3 modes in 32-byte sectors)
+  int worders = 0;  // word 7 holds the write orders of the tile form (form 2)
   int lpt_kappa = 0;                               // partition 1: blocks per mode
   std::vector<std::vector<int64_t>> lpt_load;      // partition 1: nonzeros per block
   std::vector<std::vector<int32_t>> lpt_empty;     // partition 1: rows with no nonzero
@@ -150,6 +153,10 @@ int cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return spm::cuda_fail(_e, #call); \
   } while (0)
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device (once per kernel and device; thread-safe).
+int ensure_dyn_smem(const void* kernel, size_t bytes, const char* what);
+
 // ---- host planning (plan_host.cpp) ----
 int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int nblk_opt);
 int plan_keys(spmttkrp_plan* p, const int64_t* coo, const float* vals,
@@ -158,6 +165,12 @@ int plan_partitions(spmttkrp_plan* p, int nblk_opt);
 // ---- device planning (plan_device.cu) ----
 int build_device_orders(spmttkrp_plan* p, const std::vector<std::vector<int32_t>>& key,
                         const float* vals, uint8_t* elems, int32_t* const* next_pos);
+// Write orders of the tile form (3 modes, 32-byte nonzeros carrying remap ids):
+// for every mode m and every tile of kTileNnz positions of its order, the
+// tile-local indices sorted by destination (next_pos_m), stored 10 bits per mode
+// in word 7 of the nonzero occupying each slot.  `elems` is the copy in mode-0
+// order.
+int build_write_orders(spmttkrp_plan* p, uint8_t* elems);
 int default_tile(int es);
 int partition_mode(const spmttkrp_plan* p, int n, int nblk, ModeHost* out);
 int default_nblk(int64_t nnz, int num_sms, int variant);
@@ -187,8 +200,17 @@ struct MttkrpArgs {
   int alpha_word;          // > 0: int32 word of a stored nonzero holding its position in
                            // the next mode's order (the remap id carried in the
                            // element); 0: the next_pos array
+  unsigned long long wait_ns;  // limit of the first bounded wait that gives up
+                               // (0 = the default 2 s); draining copies in flight
+                               // after a give-up always uses the default
+  int stall_test;          // test only: each warp's first wait is on a barrier that
+                           // nothing completes, so it gives up after wait_ns
+  int64_t nnz;             // nonzeros of the working copy (form 2 stages whole tiles)
+  int grid_ctas;           // form 2: persistent CTAs (0 = one per block)
 };
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
+// the tile form (form 2) covers 3 modes, 32-byte nonzeros carrying remap ids, R 16/32/64
+bool tile_form_supported(int nmodes, int es, int alpha_word, int R);
 int launch_fixup(const float* part, const SplitRow* splits, int nsplit, int nchunk,
                  float* chunk_sums, float* out, int64_t out_rows, int R, const float* scale,
                  cudaStream_t s);

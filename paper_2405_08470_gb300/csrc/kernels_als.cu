@@ -432,12 +432,9 @@ template <int CC>
 static int solve_cc(const float* M, float* U, const float* vinv, int64_t I, int R,
                     double* colsq, const int* status, int nb, cudaStream_t s) {
   const size_t smem = R <= 128 ? (size_t)R * R * 4 : 0;
-  static bool configured = false;
-  if (!configured) {
-    cudaFuncSetAttribute(als_solve_kernel<CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         128 * 128 * 4);
-    configured = true;
-  }
+  int st = ensure_dyn_smem((const void*)als_solve_kernel<CC>, 128 * 128 * 4,
+                           "cudaFuncSetAttribute(als_solve)");
+  if (st) return st;
   als_solve_kernel<CC><<<nb, 256, smem, s>>>(M, U, vinv, I, R, colsq, status);
   return SPM_OK;
 }

@@ -6,6 +6,7 @@ namespace spm {
 
 int launch_mttkrp_f32(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s);
 int launch_mttkrp_bf16(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s);
+int launch_mttkrp_tile(const MttkrpArgs& a, cudaStream_t s);
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -29,6 +30,17 @@ size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype, int stages) {
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s) {
   if (a.nblk <= 0) return SPM_OK;
   LaneCfg c = cfg_for(a);
+  if (a.variant == 2) {
+    // the tile form needs 16-byte aligned factors and output; otherwise form 0
+    bool al = aligned16(a.out);
+    for (int k = 0; k < a.nmodes; ++k)
+      if (k != a.mode) al = al && aligned16(a.factors[k]);
+    if (al && tile_form_supported(a.nmodes, a.es, a.alpha_word, a.R) && a.no_fill == 0)
+      return launch_mttkrp_tile(a, s);
+    MttkrpArgs b = a;
+    b.variant = 0;
+    return a.dtype == SPM_DTYPE_BF16 ? launch_mttkrp_bf16(b, c, s) : launch_mttkrp_f32(b, c, s);
+  }
   return a.dtype == SPM_DTYPE_BF16 ? launch_mttkrp_bf16(a, c, s) : launch_mttkrp_f32(a, c, s);
 }
 

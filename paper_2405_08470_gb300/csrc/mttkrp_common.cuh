@@ -161,8 +161,11 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Bounded wait on an mbarrier phase: gives up after ~2 s and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // default bounded-wait limit
+
+// Bounded wait on an mbarrier phase: gives up after limit_ns and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
   const uint32_t a = smem_u32(bar);
   const uint64_t t0 = global_ns();
   while (true) {
@@ -175,7 +178,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (global_ns() - t0 > 2000000000ull) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 

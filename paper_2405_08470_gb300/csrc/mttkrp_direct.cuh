@@ -279,13 +279,8 @@ int launch_direct(const MttkrpArgs& a, int L, cudaStream_t s) {
   const int NG = (kThreads / 32) * (32 / L);
   const size_t smem = direct_smem_bytes(a.R, NG);
   auto kfn = mttkrp_direct_kernel<NT, T, VW, RC, U>;
-  static size_t configured = 0;
-  if (configured < smem) {
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max<size_t>(smem, 48 * 1024));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(direct)");
-    configured = std::max<size_t>(smem, 48 * 1024);
-  }
+  int st = ensure_dyn_smem((const void*)kfn, smem, "cudaFuncSetAttribute(direct)");
+  if (st) return st;
   kfn<<<a.nblk, kThreads, smem, s>>>(a, L);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "mttkrp_direct_kernel launch");

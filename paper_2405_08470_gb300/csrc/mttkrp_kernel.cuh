@@ -61,7 +61,7 @@ __host__ __device__ inline WarpLayout warp_layout(int es, int tw, int R, int G, 
   o += (size_t)2 * G * 4;
   o = (o + 7) & ~(size_t)7;
   l.mbar = o;
-  o += (size_t)stages * 8;
+  o += (size_t)(stages + 1) * 8;  // the ring, plus one barrier only the stall test waits on
   l.total = (o + 127) & ~(size_t)127;
   return l;
 }
@@ -203,12 +203,13 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
   };
 
   if (lane == 0) {
-    for (int b = 0; b < S; ++b) mbar_init(&mbar[b], G);
+    for (int b = 0; b <= S; ++b) mbar_init(&mbar[b], G);  // mbar[S]: never completed
     fence_mbar_init();
   }
   __syncwarp();
   if (leader)
     for (int q = 0; q < S - 1 && q < ntiles; ++q) issue(q);
+  const unsigned long long wait_ns = a.wait_ns ? a.wait_ns : kWaitLimitNs;
 
   auto rank_of = [&](int j) -> int {
     if constexpr (VW > 1) return sub * VW + j;
@@ -459,7 +460,10 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
   int issued = min(ntiles, S - 1);
   for (int t = 0; t < ntiles; ++t) {
     const int st = t % S;
-    const bool ok = mbar_wait_bounded(&mbar[st], (uint32_t)((t / S) & 1));
+    // the stall test waits first on mbar[S], which no copy and no thread completes
+    const bool stall = a.stall_test && t == 0;
+    const bool ok = mbar_wait_bounded(stall ? &mbar[S] : &mbar[st],
+                                      stall ? 0u : (uint32_t)((t / S) & 1), wait_ns);
     if (!__all_sync(0xffffffffu, ok)) {
       // a bulk copy did not complete in time: record it, wait (bounded) for
       // the copies still in flight, and leave without writing anything else
@@ -581,13 +585,8 @@ int launch_warp_kernel(const MttkrpArgs& a0, int L, cudaStream_t s) {
   a.tile = warp_tile_for(a0.tile, G);
   const size_t smem = (size_t)kWarps * warp_layout(a.es, a.tile, a.R, G, a.stages).total;
   auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U, MODE, ESB>;
-  static size_t configured = 0;  // per instantiation: raise the dynamic smem limit once
-  if (configured < smem) {
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max<size_t>(smem, 48 * 1024));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mttkrp_warp)");
-    configured = std::max<size_t>(smem, 48 * 1024);
-  }
+  int st = ensure_dyn_smem((const void*)kfn, smem, "cudaFuncSetAttribute(mttkrp_warp)");
+  if (st) return st;
   const int grid = (a.nblk + kWarps - 1) / kWarps;
   kfn<<<grid, kThreads, smem, s>>>(a, L);
   cudaError_t e = cudaGetLastError();

@@ -96,20 +96,34 @@ __global__ void na_splits_kernel(const uint8_t* __restrict__ elems, int es, int6
   splits[b] = sr;
 }
 
-// Same sum as the plan's fix-up, skipping blocks without a split row.
+// Sum of each split row's block partials, one CTA per split-row entry (most
+// entries are empty and return at once).  Warp w adds the partials of blocks
+// first_blk + w, first_blk + w + 8, ... in ascending order; the eight warp sums
+// are then added in warp order, so the result is the same on every call.  A
+// head row spread over thousands of blocks is thus summed by eight warps with
+// several loads in flight each, instead of one warp walking every block.
 __global__ void __launch_bounds__(256) na_fixup_kernel(const float* __restrict__ part,
                                                        const SplitRow* __restrict__ splits,
-                                                       int nblk, float* __restrict__ out, int R) {
-  const int w = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w >= nblk) return;
-  const SplitRow sr = splits[w];
+                                                       float* __restrict__ out, int R) {
+  __shared__ float wsum[8][kMaxRank];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const SplitRow sr = splits[blockIdx.x];
   if (sr.row < 0) return;
-  for (int64_t z = (int64_t)sr.prev_row + 1; z < sr.row; ++z)
-    for (int r = lane; r < R; r += 32) out[z * R + r] = 0.f;
   for (int r = lane; r < R; r += 32) {
     float acc = 0.f;
-    for (int b = sr.first_blk; b <= sr.last_blk; ++b)
+    for (int b = sr.first_blk + w; b <= sr.last_blk; b += 8)
       acc += part[((size_t)b * 2 + ((b == sr.first_blk) ? sr.first_slot : 0)) * R + r];
+    wsum[w][r] = acc;
+  }
+  __syncthreads();
+  if (w == 0) {
+    for (int64_t z = (int64_t)sr.prev_row + 1; z < sr.row; ++z)
+      for (int r = lane; r < R; r += 32) out[z * R + r] = 0.f;
+  }
+  for (int r = threadIdx.x; r < R; r += 256) {
+    float acc = wsum[0][r];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) acc += wsum[q][r];
     out[(int64_t)sr.row * R + r] = acc;
   }
 }
@@ -139,7 +153,7 @@ extern "C" int spmttkrp_compute_noalloc(const void* elems, int64_t nnz, int nmod
   if (rank > kMaxRank)
     return fail(SPM_ERR_UNSUPPORTED, "noalloc: rank > 256 exceeds the static scratch");
   if (nnz < 0 || nnz >= (int64_t(1) << 31) - 4)
-    return fail(SPM_ERR_UNSUPPORTED, "noalloc: nnz must be in [0, 2^31)");
+    return fail(SPM_ERR_UNSUPPORTED, "noalloc: nnz must be in [0, 2^31 - 4)");
   if (nblk < 0) return fail(SPM_ERR_INVALID_ARG, "noalloc: nblk must be >= 0");
   if (nblk > kNaMaxBlocks)
     return fail(SPM_ERR_UNSUPPORTED,
@@ -204,7 +218,7 @@ extern "C" int spmttkrp_compute_noalloc(const void* elems, int64_t nnz, int nmod
                   // padding) and no device error word
   int st = launch_mttkrp(a, s);
   if (st) return st;
-  na_fixup_kernel<<<(nblk + 7) / 8, 256, 0, s>>>(sp->part, sp->splits, nblk, out, rank);
+  na_fixup_kernel<<<nblk, 256, 0, s>>>(sp->part, sp->splits, out, rank);
   na_tail_kernel<<<64, 256, 0, s>>>(ein, es, nnz, mode, out, out_rows, rank);
   SPM_CUDA(cudaGetLastError());
   return SPM_OK;

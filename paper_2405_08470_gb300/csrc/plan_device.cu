@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "mttkrp_tile.cuh"
 
 namespace spm {
 
@@ -409,6 +410,83 @@ int build_device_orders(spmttkrp_plan* p, const std::vector<std::vector<int32_t>
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "device plan build kernels");
   SPM_CUDA(cudaStreamSynchronize(s));
+  return SPM_OK;
+}
+
+}  // namespace spm
+
+// ---------------------------------------------------------------------------
+// Write orders of the tile form.
+
+namespace spm {
+namespace {
+
+// One CTA per tile of mode m's order: sort the tile's (next_pos, local index)
+// pairs by next_pos (bitonic network in shared memory; next_pos values are
+// distinct) and store, for slot j, the local index of the j-th smallest.
+__global__ void __launch_bounds__(256) write_order_kernel(const int32_t* __restrict__ next_pos,
+                                                          int64_t n,
+                                                          uint16_t* __restrict__ worder) {
+  constexpr int P = 1024;  // the network's size: kTileNnz rounded up to a power of two
+  static_assert(kTileNnz <= P, "tile larger than the sorting network");
+  __shared__ unsigned long long key[P];
+  const int64_t base = (int64_t)blockIdx.x * kTileNnz;
+  const int len = (int)min((int64_t)kTileNnz, n - base);
+  for (int i = threadIdx.x; i < P; i += blockDim.x)
+    key[i] = i < len ? (((unsigned long long)(uint32_t)next_pos[base + i] << 10) | (unsigned)i)
+                     : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long x = key[i], y = key[ixj];
+          const bool up = (i & k) == 0;
+          if (up ? (x > y) : (x < y)) {
+            key[i] = y;
+            key[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < len; i += blockDim.x)
+    worder[base + i] = (uint16_t)(key[i] & 1023u);
+}
+
+// Word 7 of each nonzero (copy in mode-0 order): the write orders of the slots
+// it occupies in the three orders (its position p in mode 0, alpha_1, alpha_2).
+__global__ void write_order_fill_kernel(uint8_t* __restrict__ elems, int64_t n,
+                                        const uint16_t* __restrict__ w0,
+                                        const uint16_t* __restrict__ w1,
+                                        const uint16_t* __restrict__ w2) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  uint32_t* e = reinterpret_cast<uint32_t*>(elems + q * 32);
+  const uint32_t a1 = e[5] & kAlphaMask, a2 = e[6] & kAlphaMask;
+  e[kTileWordW] = (uint32_t)w0[q] | ((uint32_t)w1[a1] << 10) | ((uint32_t)w2[a2] << 20);
+}
+
+}  // namespace
+
+int build_write_orders(spmttkrp_plan* p, uint8_t* elems) {
+  if (!(p->N == 3 && p->es == 32 && p->alpha) || p->nnz <= 0) return SPM_OK;
+  const int64_t n = p->nnz;
+  cudaStream_t s = p->stream;
+  Scratch sc;
+  uint16_t* w;
+  int st = sc.alloc(&w, (size_t)3 * n);
+  if (st) return st;
+  const unsigned tiles = (unsigned)((n + kTileNnz - 1) / kTileNnz);
+  for (int m = 0; m < 3; ++m)
+    write_order_kernel<<<tiles, 256, 0, s>>>(p->md[(size_t)m].next_pos, n, w + (size_t)m * n);
+  write_order_fill_kernel<<<grid_for(n, 256), 256, 0, s>>>(elems, n, w, w + n, w + 2 * n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "write-order kernels");
+  SPM_CUDA(cudaStreamSynchronize(s));
+  p->worders = 1;
   return SPM_OK;
 }
 

@@ -178,3 +178,17 @@ def test_check_argument_errors_need_no_device():
         p.check()
     assert ei.value.status == -8
     p.close()
+
+
+def test_binding_rejects_bad_tensors_before_the_c_abi():
+    """The binding checks device, dtype, shape and layout of every tensor before a
+    pointer reaches the C ABI (a host-only plan: nothing would run anyway)."""
+    import torch
+    coo, vals = synth.make_coo((20, 10, 5), 200, (0.0, 0.0, 0.0), seed=2)
+    p = _host_plan(coo.numpy(), vals.numpy(), (20, 10, 5))
+    F = [torch.zeros(d, 4) for d in (20, 10, 5)]
+    with pytest.raises(ValueError, match="CUDA device"):
+        p.compute(0, F, torch.zeros(20, 4))
+    with pytest.raises(ValueError, match="expected 3 factors"):
+        p.sweep(F[:2], F)
+    p.close()

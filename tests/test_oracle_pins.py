@@ -268,6 +268,52 @@ def test_alg1_remap_ids_are_a_permutation_grouped_by_block():
     assert np.all(np.diff(blk_in_order) >= 0)
 
 
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_alg1_remap_ids_within_block_order_is_canonical(N):
+    """Section 3.4 orders the hyperedges by partition id; inside a block the
+    reading is the canonical K_n order.  Pinned against Python ``sorted`` over
+    explicit (block, K_n) tuples, and against the independently pinned
+    canonical order filtered block by block: a reversed, rotated or shifted key
+    inside a block fails both."""
+    rng = np.random.default_rng(90 + N)
+    for trial in range(4):
+        coo, vals, dims = tiny_tensor(rng, N, maxdim=6)
+        for n in range(N):
+            for kappa in (2, 3, 4):
+                rid = O.lpt_remap_ids(coo, n, kappa)
+                deg = np.bincount(coo[:, n], minlength=int(coo[:, n].max()) + 1)
+                assign, _ = O.lpt_partition(deg, kappa)
+                blk = assign[coo[:, n]]
+                rows = [tuple(int(x) for x in r) for r in coo]
+                brute = sorted(range(len(rows)),
+                               key=lambda e: (int(blk[e]),) +
+                               tuple(rows[e][(n - j) % N] for j in range(N)))
+                order = np.argsort(rid)
+                assert np.array_equal(order, np.asarray(brute)), (N, n, kappa)
+                canon = O.brute_canonical_order(coo, n)
+                by_block = [e for b in range(kappa) for e in canon if blk[e] == b]
+                assert np.array_equal(order, np.asarray(by_block)), (N, n, kappa)
+
+
+@pytest.mark.parametrize("tile", [1, 3, 7, 960])
+def test_tile_write_order_visits_destinations_in_increasing_order(tile):
+    """Within every tile the write order is a permutation of the tile's local
+    indices along which next_pos strictly increases; next_pos values are
+    distinct, so these two properties fix it."""
+    rng = np.random.default_rng(tile)
+    for N in (2, 3, 4):
+        coo, vals, dims = tiny_tensor(rng, N, maxdim=7, density=0.5)
+        for n in range(N):
+            w = O.tile_write_order(coo, n, tile)
+            npos = O.next_pos(coo, n)
+            for base in range(0, len(npos), tile):
+                seg = [int(x) for x in npos[base:base + tile]]
+                got = [int(x) for x in w[base:base + len(seg)]]
+                assert sorted(got) == list(range(len(seg)))
+                along = [seg[j] for j in got]
+                assert all(x < y for x, y in zip(along, along[1:]))
+
+
 def test_flycoo_memory_formula():
     # Section 3.5.1: N log2|X| + sum log2 I_h + value bits
     assert O.flycoo_bits(2 ** 20, [2 ** 10] * 3) == pytest.approx(3 * 20 + 30 + 32)

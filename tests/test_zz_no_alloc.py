@@ -3,9 +3,10 @@
 It serves callers that cannot call cudaMalloc (code in an allocator-free region
 of a host framework, or a process whose device memory belongs to another pool):
 they cannot create a plan, so they pass every buffer in and the call keeps its
-scratch in a fixed static device array.  Checked here against the existing
-plan-based entry point, on two calls in a row (the static scratch keeps the
-previous call's contents).  This file is collected last on purpose.
+scratch in a fixed static device array.  Checked here against the FP64 oracle
+directly and against the existing plan-based entry point, on two calls in a row
+(the static scratch keeps the previous call's contents).  This file is collected
+last on purpose.
 """
 import ctypes
 
@@ -66,6 +67,7 @@ def test_noalloc_matches_plan_entry_point_twice(dims, R, dtype, nblk):
     c, v = coo.numpy(), vals.numpy()
     tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
     F = [f.to(tdt).cuda() for f in synth.make_factors(dims, R, seed=7)]
+    Fo = [f.float().cpu().numpy().astype(np.float64) for f in F]   # as the GPU reads them
     plan = Plan(c, v, dims, R, dtype=dtype)
     for n in range(N):
         want = torch.empty(dims[n], R, device="cuda")
@@ -73,6 +75,7 @@ def test_noalloc_matches_plan_entry_point_twice(dims, R, dtype, nblk):
         elems = device_elements(c, v, n)
         npos = torch.from_numpy(O.next_pos(c, n).astype(np.int32)).cuda()
         nxt = device_elements(c, v, (n + 1) % N).cpu().numpy()
+        exact = O.mttkrp(c, v, dims, Fo, n)             # Eq. 1 in FP64
         for rep in range(2):                           # two calls in a row
             out = torch.full((dims[n], R), float("nan"), device="cuda")
             eout = torch.zeros_like(elems)
@@ -82,6 +85,7 @@ def test_noalloc_matches_plan_entry_point_twice(dims, R, dtype, nblk):
             torch.cuda.synchronize()
             got = out.cpu().numpy().astype(np.float64)
             assert np.all(np.isfinite(got)), (n, rep)
+            assert O.relerr(got, exact) <= 1e-5, (n, rep, O.relerr(got, exact))
             assert O.relerr(got, want.cpu().numpy()) <= 1e-5, (n, rep)
             assert np.array_equal(eout.cpu().numpy(), nxt), (n, rep)
     plan.close()
@@ -97,3 +101,30 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     big = [torch.empty(d, 257, device="cuda") for d in dims]
     assert call(elems, 100, dims, 0, 257, 0, big, torch.empty(10, 257, device="cuda")) == -6
     assert b"4096" in lib().spmttkrp_last_error() or b"256" in lib().spmttkrp_last_error()
+
+
+def test_noalloc_head_row_over_every_block():
+    """One row holding most nonzeros is split over all 4096 blocks; its partials
+    are summed by the fix-up in fixed order, equal to the oracle and the same on
+    two calls."""
+    dims, R = (50, 3000, 2000), 32
+    rng = np.random.default_rng(3)
+    nnz = 200_000
+    c = np.stack([np.where(rng.random(nnz) < 0.9, 7, rng.integers(0, 50, nnz)),
+                  rng.integers(0, 3000, nnz), rng.integers(0, 2000, nnz)], 1)
+    c = np.unique(c, axis=0)
+    c = c[rng.permutation(c.shape[0])]
+    v = rng.random(c.shape[0]).astype(np.float32)
+    F = [f.cuda() for f in synth.make_factors(dims, R, seed=9)]
+    Fo = [f.cpu().numpy().astype(np.float64) for f in F]
+    elems = device_elements(c, v, 0)
+    exact = O.mttkrp(c, v, dims, Fo, 0)
+    outs = []
+    for rep in range(2):
+        out = torch.full((dims[0], R), float("nan"), device="cuda")
+        st = call(elems, c.shape[0], dims, 0, R, 0, F, out, nblk=4096)
+        assert st == 0, lib().spmttkrp_last_error()
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy())
+        assert O.relerr(outs[-1].astype(np.float64), exact) <= 1e-5, rep
+    assert np.array_equal(outs[0], outs[1])
