@@ -61,11 +61,14 @@ def parse():
                     help="0: contiguous split with heavy-row splitting; 1: Algorithm 1 (LPT)")
     ap.add_argument("--keep-base", action="store_true",
                     help="keep the mode-0 copy resident: the last mode's pass writes no remap")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the BF16 sweep, CP-loss and CP-ALS measurements")
+    ap.add_argument("--no-workload-extras", action="store_true",
+                    help="skip the lines on the other workloads (4-mode FP32/BF16, CP loss "
+                         "on the completion tensor, CP-ALS on the 5- and 6-mode tensors) "
+                         "and the memory-ceiling probe")
     return ap.parse_args()
 
 
@@ -181,8 +184,8 @@ class ClockSampler:
 
 
 # sources that define and launch the fused spMTTKRP + remap kernel
-KERNEL_SOURCES = ("mttkrp_common.cuh", "mttkrp_kernel.cuh", "mttkrp_direct.cuh", "kernels_f32.cu",
-                  "kernels_bf16.cu", "kernels_misc.cu")
+KERNEL_SOURCES = ("mttkrp_common.cuh", "mttkrp_kernel.cuh", "mttkrp_direct.cuh", "mttkrp_tile.cuh",
+                  "kernels_f32.cu", "kernels_bf16.cu", "kernels_tile.cu", "kernels_misc.cu")
 
 
 def kernel_digest():
@@ -194,9 +197,13 @@ def kernel_digest():
 
 
 def ncu_traffic(workload, R, dtype, nnz, info):
-    """DRAM bytes per launch of the fused kernel from a committed ncu summary, if its
-    kernel digest matches the current sources and the run has the captured
-    configuration (size, blocks, tile, ring depth, stride, plan options); else null."""
+    """DRAM bytes per launch of the fused kernel from a committed ncu summary: bytes
+    measured on a smaller tensor of the same shape (one kernel, its three mode
+    launches), scaled to this run's nonzero count (per-nonzero traffic: the stream,
+    the scattered copy and the factor-row misses all grow with the nonzeros).
+    Used only while the kernel sources hash to the captured digest and the run has
+    the captured configuration (blocks per SM, kernel form, stride, plan options);
+    else null."""
     path = os.path.join(PROFILES, "mttkrp_remap_traffic.json")
     if not os.path.exists(path):
         return None
@@ -206,20 +213,20 @@ def ncu_traffic(workload, R, dtype, nnz, info):
         return None
     if d.get("kernel_digest") != kernel_digest():
         return None
-    key = f"{workload}_R{R}_{dtype}"
-    e = d.get("entries", {}).get(key)
+    e = d.get("entries", {}).get(f"{workload}_R{R}_{dtype}")
     if not e:
         return None
     cfg = e.get("config", {})
-    if cfg.get("nnz") != nnz or any(info.get(k) != v for k, v in cfg.items() if k != "nnz"):
+    if any(info.get(k) != v for k, v in cfg.items()):
         return None
-    return e.get("dram_bytes_per_launch_full")
+    return e["dram_bytes_per_nonzero_per_launch"] * nnz
 
 
-def cpu_oracle_sample(coo_h, vals_h, dims, R, target_s, seed):
-    """The multi-threaded C FP64 oracle on the first S nonzeros (draw order) of the
-    workload, all modes: median of 3 sweeps on all host threads and on one thread.  S is
-    sized so that a one-thread sweep takes about target_s / 4 seconds."""
+def cpu_oracle_full(coo_h, vals_h, dims, R, seed, one_thread_seconds=4.0):
+    """The multi-threaded C FP64 oracle on ALL nonzeros of the workload, every mode,
+    on all host threads (median of 3 sweeps).  A one-thread figure is timed on the
+    first S nonzeros only (S sized to about `one_thread_seconds` per sweep) and
+    scaled by nnz / S; it is labelled as such."""
     from oracle import ref_c
     F = [f.numpy().astype(np.float64) for f in synth.make_factors(dims, R, seed=seed)]
     nnz = coo_h.shape[0]
@@ -234,36 +241,37 @@ def cpu_oracle_sample(coo_h, vals_h, dims, R, target_s, seed):
             per.append(time.perf_counter() - t0)
         return per
 
-    S = min(nnz, 200_000)
-    while True:
-        dt = sum(sweep(S, 1))
-        if dt >= target_s / 8 or S >= nnz:
-            break
-        S = min(nnz, int(S * max(2.0, target_s / 4 / max(dt, 1e-3))))
     med = lambda runs: [float(np.median([r[n] for r in runs])) for n in range(N)]  # noqa: E731
-    one = med([sweep(S, 1) for _ in range(3)])
-    allt = med([sweep(S, 0) for _ in range(3)])
-    scale = 1e3 * nnz / S
-    return {"value": sum(allt) * scale, "unit": "ms", "cores": ref_c.threads(), "kind": "oracle",
-            "sample": f"first {S} nonzeros (draw order) of the workload, all {N} modes, C FP64 "
-                      f"oracle (OpenMP, rows in parallel), median of 3, time scaled by nnz/{S}",
-            "per_mode_ms": [t * scale for t in allt],
-            "one_thread": {"value": sum(one) * scale, "per_mode_ms": [t * scale for t in one]}}
+    allt = med([sweep(nnz, 0) for _ in range(3)])
+    S = min(nnz, 1_000_000)
+    dt = sum(sweep(S, 1))
+    S = min(nnz, max(S, int(S * one_thread_seconds / max(dt, 1e-3))))
+    one = med([sweep(S, 1)])
+    return {"value": sum(allt) * 1e3, "unit": "ms", "cores": ref_c.threads(), "kind": "oracle",
+            "sample": f"all {nnz} nonzeros of the workload, all {N} modes, C FP64 oracle "
+                      f"(OpenMP over output rows), median of 3 sweeps",
+            "per_mode_ms": [t * 1e3 for t in allt],
+            "one_thread": {"value": sum(one) * 1e3 * nnz / S,
+                           "per_mode_ms": [t * 1e3 * nnz / S for t in one],
+                           "sample": f"first {S} nonzeros (draw order), one sweep, time "
+                                     f"scaled by nnz/{S}"}}
 
 
 def run_reference(args, rank, world):
-    """The oracle as it stands, timed on the host cores (bounded sample per step)."""
+    """The oracle as it stands (the C FP64 spMTTKRP, OpenMP over rows), timed on the
+    host cores on the whole workload: every step is a full all-mode sweep over all
+    nonzeros.  A sweep takes seconds, so the run keeps at most 2 timed steps and 1
+    warm-up step (the line states the numbers it ran and the ones requested)."""
     if rank != 0:
         return
     spec = synth.workload(args.workload)
     R = args.rank or spec.ranks[0]
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     nnz_full = args.nnz or spec.nnz
-    sample_nnz = min(4_000_000, nnz_full)
-    coo, vals = synth.make_coo(spec.dims, nnz_full, spec.skew, spec.seed, device=dev) \
-        if dev == "cuda" else synth.make_coo(spec.dims, sample_nnz, spec.skew, spec.seed)
-    coo_h = coo[:sample_nnz].cpu().numpy()
-    vals_h = vals[:sample_nnz].cpu().numpy()
+    coo, vals = synth.make_coo(spec.dims, nnz_full, spec.skew, spec.seed, device=dev)
+    coo_h = coo.cpu().numpy()
+    vals_h = vals.cpu().numpy()
+    del coo, vals
     from oracle import ref_c
     F = [f.numpy().astype(np.float64) for f in synth.make_factors(spec.dims, R, seed=synth.factor_seed(
         WORKLOAD_INDEX[args.workload]))]
@@ -274,24 +282,27 @@ def run_reference(args, rank, world):
         for n in range(N):
             ref_c.mttkrp(coo_h, vals64, spec.dims, F, n)
 
-    for _ in range(args.warmup):
+    steps, warm = max(1, min(args.steps, 2)), min(args.warmup, 1)
+    for _ in range(warm):
         step()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
-    dt = (time.perf_counter() - t0) / args.steps
-    ms_full = dt * 1e3 * nnz_full / coo_h.shape[0]
+    ms = (time.perf_counter() - t0) / steps * 1e3
     line = {
-        "impl": "reference", "metric": "all-mode spMTTKRP ms per sweep", "value": ms_full,
-        "unit": "ms", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_full, "higher_is_better": False, "scaling": "weak",
+        "impl": "reference", "metric": "all-mode spMTTKRP ms per sweep", "value": ms,
+        "unit": "ms", "n_gpus": args.gpus, "steps": steps, "warmup": warm,
+        "steps_requested": args.steps, "warmup_requested": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": spec.name, "rank": R, "nnz": nnz_full},
-        "cpu_baseline": {"value": ms_full, "unit": "ms", "cores": ref_c.threads(), "kind": "oracle",
-                         "sample": f"first {coo_h.shape[0]} nonzeros (draw order) of the workload, "
-                                   f"all {N} modes per step, C FP64 oracle (OpenMP), time scaled "
-                                   f"by nnz"},
-        "e2e": {"value": ms_full, "unit": "ms", "h2d_bytes_per_step": 0,
+        "config": {"workload": spec.name if nnz_full == spec.nnz else
+                   f"{spec.name}; reduced to {nnz_full} nonzeros",
+                   "dims": list(spec.dims), "nnz": nnz_full, "rank": R},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": ref_c.threads(), "kind": "oracle",
+                         "sample": f"all {coo_h.shape[0]} nonzeros of the workload, all {N} "
+                                   f"modes per step, C FP64 oracle (OpenMP over output rows); "
+                                   f"{steps} timed step(s) after {warm} warm-up"},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -471,6 +482,191 @@ def extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, strea
     return res
 
 
+def _sample_rows(dim, k, seed):
+    g = np.random.default_rng(seed)
+    return np.unique(np.concatenate([g.integers(0, dim, k), [0, dim - 1]]))
+
+
+def _rows_err(got_rows, want_rows):
+    den = float(np.linalg.norm(want_rows))
+    return float(np.linalg.norm(got_rows - want_rows)) / den if den else 0.0
+
+
+def _guard(name, fn, res):
+    """Runs one extra measurement; a failure is recorded in the line, not raised."""
+    try:
+        res[name] = fn()
+    except Exception as ex:  # noqa: BLE001 - report and keep the rest of the line
+        res[name] = {"error": f"{type(ex).__name__}: {ex}"}
+    torch.cuda.empty_cache()
+
+
+def memory_ceiling(nnz, stream, reps):
+    """Memory-system ceilings for the remap's access pattern on this GPU: a copy,
+    scattered writes and gathered reads of nnz 32-byte records (random permutation
+    of runs of 1, 2 or 4 consecutive records; 4 records = one 128-byte line)."""
+    from paper_2405_08470_gb300.binding import memprobe
+    a = torch.empty(nnz * 8, dtype=torch.int32, device="cuda")
+    b = torch.empty_like(a)
+    a.fill_(1)
+    out = {"records": nnz, "record_bytes": 32, "buffer_gb": nnz * 32 / 1e9}
+    for name, kind, run in (("copy", 0, 1), ("scatter_run1", 1, 1), ("scatter_run2", 1, 2),
+                            ("scatter_run4", 1, 4), ("gather_run1", 2, 1)):
+        if nnz % run:
+            continue
+        ms = time_events(lambda: memprobe(kind, a, b, nnz, run, stream), reps, stream)
+        out[name] = {"ms": ms, "gbs_read_plus_write": 2 * nnz * 32 / (ms * 1e-3) / 1e9,
+                     "g_records_per_s": nnz / (ms * 1e-3) / 1e9}
+    del a, b
+    return out
+
+
+def c3_precision(args, stream, reps):
+    """Configuration 3: 4-mode 1000000x20000x2000x500, 150M nonzeros, R=32: one
+    all-mode sweep with FP32 and with BF16 factors (autotuned), each with its
+    per-mode normwise error against the FP64 oracle on sampled output rows (BF16:
+    against the oracle on the BF16-rounded factors, the accumulation error, and
+    on the FP32 factors, the quantisation error)."""
+    import oracle as O
+    from paper_2405_08470_gb300 import Plan
+    spec = synth.workload("c3")
+    R = 32
+    coo, vals = synth.make_coo(spec.dims, spec.nnz, spec.skew, spec.seed, device="cuda")
+    coo_h, vals_h = coo.cpu().numpy(), vals.cpu().numpy()
+    del coo, vals
+    torch.cuda.empty_cache()
+    F = synth.make_factors(spec.dims, R, seed=synth.factor_seed(2), device="cuda")
+    F64 = [f.double().cpu().numpy() for f in F]
+    Fq64 = [f.to(torch.bfloat16).double().cpu().numpy() for f in F]
+    rows = [_sample_rows(d, 24, 30 + n) for n, d in enumerate(spec.dims)]
+    want = [O.mttkrp_rows(coo_h, vals_h, F64, n, rows[n]) for n in range(4)]
+    wantq = [O.mttkrp_rows(coo_h, vals_h, Fq64, n, rows[n]) for n in range(4)]
+    out = {"workload": spec.name, "rank": R, "nnz": spec.nnz,
+           "rows_checked_per_mode": [len(r) for r in rows]}
+    for dt in ("f32", "bf16"):
+        Fd = [f.to(torch.bfloat16) for f in F] if dt == "bf16" else F
+        p = Plan(coo_h, vals_h, spec.dims, R, dtype=dt)
+        outs = [torch.empty(d, R, device="cuda") for d in spec.dims]
+        p.autotune(Fd, outs)
+        ms = time_events(lambda: p.sweep(Fd, outs, graph=True), reps, stream)
+        got = [outs[n].cpu().numpy()[rows[n]].astype(np.float64) for n in range(4)]
+        e = {"ms_per_sweep": ms, "nblk": p.info()["nblk"], "kernel_form": p.info()["variant"]}
+        if dt == "f32":
+            e["err_vs_fp64_per_mode"] = [_rows_err(got[n], want[n]) for n in range(4)]
+        else:
+            e["err_vs_fp64_bf16_factors_per_mode"] = [_rows_err(got[n], wantq[n])
+                                                      for n in range(4)]
+            e["err_vs_fp64_fp32_factors_per_mode"] = [_rows_err(got[n], want[n])
+                                                      for n in range(4)]
+        out[dt] = e
+        p.close()
+        del outs
+        torch.cuda.empty_cache()
+    return out
+
+
+def c5_cp_loss(args, stream, reps):
+    """Configuration 5: CP completion, 2000000x2000000x100000 with 200M observed
+    entries (Zipf 1.1), targets from a planted rank-8 model plus N(0, 0.01) noise,
+    fitted factors N(0,1)*0.1 at R=64: CP-loss forward + backward (the autograd
+    function) in nonzeros per second with FP32 and BF16 factors, each with its
+    gradient error against the FP64 oracle on sampled rows of every mode."""
+    import oracle as O
+    from paper_2405_08470_gb300 import Plan
+    from paper_2405_08470_gb300.cp import CPLoss
+    spec = synth.workload("c5")
+    R = 64
+    coo, _ = synth.make_coo(spec.dims, spec.nnz, spec.skew, spec.seed, device="cuda")
+    x = synth.make_planted_targets(coo, spec.dims, 8, 0.1, spec.seed + 1)
+    coo_h, x_h = coo.cpu().numpy(), x.cpu().numpy()
+    del coo, x
+    torch.cuda.empty_cache()
+    F = synth.make_factors(spec.dims, R, seed=synth.factor_seed(4), device="cuda", scale=0.1)
+    rows = [_sample_rows(d, 16, 50 + n) for n, d in enumerate(spec.dims)]
+    out = {"workload": spec.name + ", planted rank-8 targets + N(0,0.01) noise", "rank": R,
+           "nnz": spec.nnz, "rows_checked_per_mode": [len(r) for r in rows]}
+    G64 = [O.cp_loss_grad_rows(coo_h, x_h, [f.double().cpu().numpy() for f in F], n, rows[n])
+           for n in range(3)]
+    for dt in ("f32", "bf16"):
+        tdt = torch.bfloat16 if dt == "bf16" else torch.float32
+        p = Plan(coo_h, x_h, spec.dims, R, dtype=dt)
+        Fg = [f.to(tdt).requires_grad_(True) for f in F]
+        scratch = [torch.empty(d, R, device="cuda") for d in spec.dims]
+        p.autotune([f.detach() for f in Fg], scratch)
+        del scratch
+
+        def step():
+            for f in Fg:
+                f.grad = None
+            CPLoss.apply(p, *Fg).backward()
+
+        ms = time_events(step, reps, stream)
+        # FP32 gradients straight from the engine (autograd casts BF16 ones to BF16)
+        g32 = [torch.empty(d, R, device="cuda") for d in spec.dims]
+        lossv = torch.empty((), device="cuda")
+        fs = [f.detach() for f in Fg]
+        p.loss_fwd(fs, lossv)
+        p.loss_bwd(fs, torch.ones((), device="cuda"), g32)
+        got = [g32[n].cpu().numpy()[rows[n]].astype(np.float64) for n in range(3)]
+        e = {"ms_fwd_bwd": ms, "nnz_per_s": spec.nnz / (ms * 1e-3), "loss": float(lossv)}
+        if dt == "f32":
+            e["grad_err_vs_fp64_per_mode"] = [_rows_err(got[n], G64[n]) for n in range(3)]
+        else:
+            Fq = [f.to(torch.bfloat16).double().cpu().numpy() for f in F]
+            Gq = [O.cp_loss_grad_rows(coo_h, x_h, Fq, n, rows[n]) for n in range(3)]
+            e["grad_err_vs_fp64_bf16_factors_per_mode"] = [_rows_err(got[n], Gq[n])
+                                                           for n in range(3)]
+            e["grad_err_vs_fp64_fp32_factors_per_mode"] = [_rows_err(got[n], G64[n])
+                                                           for n in range(3)]
+        out[dt] = e
+        p.close()
+        del Fg, g32, fs
+        torch.cuda.empty_cache()
+    return out
+
+
+def c4_als(args, stream, reps):
+    """Configuration 4: one CPD-ALS iteration (every mode's fused pass, the FP64
+    Gram Hadamard and Cholesky on the GPU, the solve and the column scaling,
+    replayed as one CUDA graph) on the 5-mode 60M and 6-mode 40M tensors at
+    R = 16, 32, 64, each plan autotuned; host-timed per iteration including the
+    read-back of the fit (median of 5 after the capture)."""
+    from paper_2405_08470_gb300 import Plan
+    out = {}
+    for name, ci in (("c4a", 3), ("c4b", 3)):
+        spec = synth.workload(name)
+        coo, vals = synth.make_coo(spec.dims, spec.nnz, spec.skew, spec.seed, device="cuda")
+        coo_h, vals_h = coo.cpu().numpy(), vals.cpu().numpy()
+        del coo, vals
+        torch.cuda.empty_cache()
+        ent = {"workload": spec.name}
+        for R in spec.ranks:
+            p = Plan(coo_h, vals_h, spec.dims, R)
+            F = synth.make_factors(spec.dims, R, seed=synth.factor_seed(ci), device="cuda")
+            scratch = [torch.empty(d, R, device="cuda") for d in spec.dims]
+            p.autotune(F, scratch)
+            t0 = time.perf_counter()
+            p.sweep(F, scratch, graph=True)
+            torch.cuda.synchronize()
+            sweep_ms = time_events(lambda: p.sweep(F, scratch, graph=True), reps, stream)
+            del scratch
+            lam = torch.empty(R, device="cuda")
+            fits = [p.als_iter(F, lam)]  # eager + capture
+            ts = []
+            for _ in range(5):
+                t0 = time.perf_counter()
+                fits.append(p.als_iter(F, lam))
+                ts.append((time.perf_counter() - t0) * 1e3)
+            ent[f"R{R}"] = {"als_iter_ms": float(np.median(ts)), "sweep_ms": sweep_ms,
+                            "fits": fits, "nblk": p.info()["nblk"],
+                            "kernel_form": p.info()["variant"]}
+            p.close()
+            del F
+            torch.cuda.empty_cache()
+        out[name] = ent
+    return out
+
+
 def main():
     args = parse()
     rank, world = dist_setup(args)
@@ -550,7 +746,8 @@ def main():
     t_roof_ms = sum(byts) / (peak * 1e9) * 1e3
     achieved = sum(byts) / (per_mode.sum() * 1e-3) / 1e9
     traffic = ncu_traffic(args.workload, R, args.dtype, nnz,
-                          dict(info, unroll=args.unroll or 8, cache_hints=args.hints))
+                          dict(info, unroll=args.unroll or 8, cache_hints=args.hints,
+                               blocks_per_sm=info["nblk"] / info["num_sms"]))
     # per-nonzero gathers counted every time (no reuse in L1/L2), for comparison
     E = 4 * N + 4
     no_reuse = sum(nnz * (E + 4 + E) + nnz * (N - 1) * R * s + spec.dims[n] * R * 4
@@ -597,10 +794,40 @@ def main():
     extra = {}
     if not args.no_extras:
         extra = extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, stream, world)
+    if e2e is not None:
+        # one shot from host data: plan build from the host COO (sorts, remap ids,
+        # partition, uploads), factors uploaded, one sweep, outputs read back
+        Fh1 = [f.cpu() for f in F]
+        plan.close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p1 = Plan(coo_h, vals_h, spec.dims, R, dtype=args.dtype, nblk=args.nblk,
+                  tile=args.tile, variant=info["variant"], element_bytes=args.element_bytes,
+                  keep_base=args.keep_base, partition=args.partition)
+        Fd1 = [f.to(dev) for f in Fh1]
+        p1.sweep(Fd1, outs)
+        Oh1 = [o.cpu() for o in outs]
+        torch.cuda.synchronize()
+        e2e["one_shot_ms"] = (time.perf_counter() - t0) * 1e3
+        e2e["one_shot_how"] = ("host COO (int64) and values to outputs on the host: plan build "
+                               "(device sorts, remap ids, write orders, partition, uploads), "
+                               "factor upload, one all-mode sweep, output download; host-timed")
+        del Oh1, Fd1, Fh1
+        plan = p1
+    plan.close()
+    del F, outs
+    torch.cuda.empty_cache()
+    if not (args.no_extras or args.no_workload_extras) and world == 1 and nnz == spec.nnz \
+            and args.workload == "c2":
+        reps = max(2, min(args.steps, 5))
+        _guard("memory_ceiling", lambda: memory_ceiling(nnz, stream, reps), extra)
+        _guard("c3_fp32_vs_bf16", lambda: c3_precision(args, stream, reps), extra)
+        _guard("cp_loss_c5", lambda: c5_cp_loss(args, stream, reps), extra)
+        _guard("cp_als_c4", lambda: c4_als(args, stream, reps), extra)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(coo_h, vals_h, spec.dims, R, args.cpu_seconds, fseed)
+        cpu = cpu_oracle_full(coo_h, vals_h, spec.dims, R, fseed)
 
     launches = info["launches_per_sweep"] * K
     if rank == 0:
@@ -614,7 +841,9 @@ def main():
                        "dims": list(spec.dims), "nnz": nnz, "rank": R,
                        "factor_dtype": args.dtype, "nblk": info["nblk"], "tile": info["tile"],
                        "kernel_form": ["warp blocks, bulk-async staged tiles",
-                                       "CTA blocks, direct runs"][info["variant"]],
+                                       "CTA blocks, direct runs",
+                                       "persistent CTAs, 960-nonzero tiles, remap stores in "
+                                       "destination order"][info["variant"]],
                        "autotuned": bool(args.autotune),
                        "unroll": args.unroll or 8, "cache_hints": args.hints,
                        "stages": info["stages"],
@@ -631,7 +860,9 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                         "kernel": "mttkrp_warp_kernel (+ splitrow_fixup, per-mode events)",
+                         "kernel": ["mttkrp_warp_kernel", "mttkrp_direct_kernel",
+                                    "mttkrp_tile_kernel"][info["variant"]] +
+                                   " (+ split-row fix-up; CUDA events around each mode)",
                          "algorithmic_bytes_per_sweep": int(sum(byts)),
                          "no_reuse_bytes_per_sweep": int(no_reuse),
                          "dram_gbs_ncu_bytes_over_event_time": (traffic * N / (per_mode.sum() * 1e-3) / 1e9
@@ -647,7 +878,6 @@ def main():
         }
         line.update(extra)
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

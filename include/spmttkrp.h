@@ -93,9 +93,12 @@ typedef struct {
                        32 = padded (up to 7 modes).  A 3-mode nonzero in 32 bytes
                        carries its remap ids in the padding (Section 3.5): its
                        positions in the three modes' orders                       */
-  int cache_hints;  /* form 0 L2 policy: -1 = none, 0 = default (= 3); bit0: the
-                       nonzero stream, remap ids and remapped copy evict first;
-                       bit1: factor rows evict last                               */
+  int cache_hints;  /* fused-kernel cache policy: -1 = none, 0 = default (= 3);
+                       bit0: the nonzero stream, remap ids and remapped copy evict
+                       first in L2; bit1: factor rows evict last in L2; bit2 (tile
+                       form only): L1 by the hot-row flags of 3-mode 32-byte
+                       nonzeros (the rows of each factor holding the most
+                       nonzeros evict last, the others first)                     */
   void* stream;     /* cudaStream_t for all work; NULL = default stream           */
   int keep_base;    /* 1 = keep the mode-0 copy resident and read-only next to the
                        two working copies (one more copy of the nonzeros): mode 0
@@ -223,10 +226,28 @@ int cp_als_iter(spmttkrp_plan_t plan, void* const* factors, float* lambda, doubl
  */
 int cp_loss_fwd(spmttkrp_plan_t plan, const void* const* factors, float* loss);
 
+/* flags for cp_loss_fwd_ex */
+enum { SPM_LOSS_FORWARD_ONLY = 1 /* no gradient will follow: the plain forward pass */ };
+
+/*
+ * cp_loss_fwd with flags.  By default (flags 0) a plan whose nonzeros are
+ * 3-mode 32-byte sectors (and whose factors are 16-byte aligned, R a multiple
+ * of 4) runs one fused pass in the working copy's current mode n: it computes
+ * the residuals, the loss, the gradient dL/dA_n (kept in the plan until the
+ * next cp_loss_bwd scales it by grad_out), and writes the residual copy
+ * directly in the mode-(n+1) order, so the backward needs N-1 passes instead
+ * of N.  SPM_LOSS_FORWARD_ONLY runs the plain forward (residual copy in mode n
+ * order, no gradient), the cheaper choice when no backward follows.  Other
+ * plans always run the plain forward.  Arguments and errors as cp_loss_fwd.
+ */
+int cp_loss_fwd_ex(spmttkrp_plan_t plan, const void* const* factors, float* loss, int flags);
+
 /*
  * Gradient of the CP loss: grads[n] = grad_out * spMTTKRP_n(residual tensor)
- * for every mode, one all-mode sweep on a remapped copy of the residuals.
- * Needs a previous cp_loss_fwd with the same factors.
+ * for every mode, one all-mode sweep on a remapped copy of the residuals (after
+ * the fused forward: the forward's mode is a scaled copy of the gradient it left,
+ * and the sweep covers the other N-1 modes).  Needs a previous cp_loss_fwd with
+ * the same factors; it consumes that forward's residuals.
  *   grad_out device, float scalar (dL_total/dL).
  *   grads    host array of nmodes device pointers, float [dims[n]][rank].
  */
@@ -255,8 +276,10 @@ enum {
   SPM_Q_INFO = 0,     /* int64[16]: nnz, nmodes, rank, elem_bytes, cur_mode, dtype,
                          tile, nblk(mode), nsplit(mode), launches per sweep,
                          device bytes, working buffer, flags (bit0 host_only, bit1
-                         variant, bit2 keep_base, bits 3-5 ring stages, bit6
-                         partition, bit7 nonzeros carry their remap ids), SMs,
+                         variant & 1, bit2 keep_base, bits 3-5 ring stages, bit6
+                         partition, bit7 nonzeros carry their remap ids, bits 8-9
+                         variant, bit10 nonzeros carry write orders, bits 11-31
+                         hot rows per factor, 0 = no hot-row flags), SMs,
                          |X|^2 (double), lanes                                      */
   SPM_Q_NEXT_POS = 1, /* int32[nnz]: next_pos of `mode`                            */
   SPM_Q_BOUNDS = 2,   /* int64[nblk+1]: block boundaries of `mode`                 */
@@ -338,6 +361,23 @@ int spmttkrp_check_elements(const void* elems, int64_t nnz, int nmodes, const in
  * nonzeros, the id word of the next mode.  Errors: INVALID_ARG, STATE
  * (host-only plan, or a failed check), INDEX_RANGE, CUDA. */
 int spmttkrp_plan_check(spmttkrp_plan_t plan);
+
+/*
+ * Memory-system probe (a measurement utility; the paper has no counterpart):
+ * one kernel over n records of 32 bytes that the caller times, for the access
+ * patterns of the dynamic remap.
+ *   kind 0  copy: dst[i] = src[i]
+ *   kind 1  scatter: dst[pi(i)] = src[i]
+ *   kind 2  gather: dst[i] = src[pi(i)]
+ * pi keeps runs of `run` consecutive records together (run 4 = one 128-byte
+ * line) and sends run q to run (A q + 12345) mod (n / run), A a fixed prime not
+ * dividing n / run (a permutation of the runs).
+ *   src, dst  device, n * 32 bytes each, 32-byte aligned, not overlapping.
+ *   run       >= 1 and dividing n.
+ *   stream    cudaStream_t (NULL = default); asynchronous.
+ * Errors: INVALID_ARG, CUDA.
+ */
+int spmttkrp_memprobe(int kind, const void* src, void* dst, int64_t n, int run, void* stream);
 
 /* Thread-local text for the last non-OK status of this thread. */
 const char* spmttkrp_last_error(void);

@@ -340,6 +340,19 @@ def tile_write_order(coo, n, tile):
     return out
 
 
+def hot_rows(coo, k, H):
+    """The H rows of mode k holding the most nonzeros (ties to the lower row id;
+    rows without nonzeros never count).  These factor rows are the ones gathered
+    most often in the other modes' passes.  Returns a sorted int64 array."""
+    col = np.asarray(coo)[:, k]
+    if col.size == 0:
+        return np.zeros(0, dtype=np.int64)
+    deg = np.bincount(col)
+    rows = np.nonzero(deg)[0]
+    order = sorted(rows.tolist(), key=lambda r: (-int(deg[r]), r))
+    return np.sort(np.asarray(order[:int(H)], dtype=np.int64))
+
+
 def flycoo_bits(nnz, dims, value_bits=32):
     """Bits per nonzero of the FLYCOO element (Section 3.5.1).
 
@@ -452,6 +465,26 @@ def cp_loss_grad(coo, vals, dims, factors):
     """dL/dA_n = mode-n spMTTKRP of the residual tensor (values m_e - x_e)."""
     _, e = cp_loss(coo, vals, factors)
     return [mttkrp(coo, e, dims, factors, n) for n in range(len(dims))]
+
+
+def cp_loss_grad_rows(coo, vals, factors, n, rows):
+    """Selected rows of dL/dA_n for workloads too large for ``cp_loss_grad``.
+
+    For every requested row i: the observed entries with i_n == i (input
+    order), their residuals m_e - x_e, and the mode-n spMTTKRP row of those
+    residuals (``mttkrp_rows``)."""
+    coo = np.asarray(coo)
+    vals = np.asarray(vals, dtype=np.float64)
+    R = np.asarray(factors[0]).shape[1]
+    out = np.zeros((len(rows), R), dtype=np.float64)
+    col = coo[:, n]
+    for j, i in enumerate(rows):
+        sel = np.nonzero(col == i)[0]
+        if sel.size == 0:
+            continue
+        r = cp_model_at(coo[sel], factors) - vals[sel]
+        out[j] = mttkrp_rows(coo[sel], r, factors, n, [i])[0]
+    return out
 
 
 # --------------------------------------------------------------------------

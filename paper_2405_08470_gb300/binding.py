@@ -85,6 +85,7 @@ def lib():
     L.spmttkrp_sweep.argtypes = [P, P, P, ctypes.c_int]
     L.cp_als_iter.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double)]
     L.cp_loss_fwd.argtypes = [P, P, P]
+    L.cp_loss_fwd_ex.argtypes = [P, P, P, ctypes.c_int]
     L.cp_loss_bwd.argtypes = [P, P, P, P]
     L.spmttkrp_autotune.argtypes = [P, P, P, ctypes.c_int]
     L.spmttkrp_plan_query.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t]
@@ -92,6 +93,7 @@ def lib():
     L.spmttkrp_check_elements.argtypes = [P, ctypes.c_int64, ctypes.c_int, I64P, ctypes.c_int,
                                           P, ctypes.c_int, P]
     L.spmttkrp_plan_check.argtypes = [P]
+    L.spmttkrp_memprobe.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, ctypes.c_int, P]
     for name in declared_functions():
         getattr(L, name).restype = ctypes.c_char_p if name == "spmttkrp_last_error" \
             else ctypes.c_int
@@ -119,6 +121,14 @@ def _stream_ptr(stream):
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream) if hasattr(stream, "cuda_stream") \
         else ctypes.c_void_p(stream)
+
+
+def memprobe(kind: int, src, dst, n: int, run: int = 1, stream=None):
+    """Queues one memory-probe kernel (0 copy, 1 scatter, 2 gather of 32-byte
+    records; see spmttkrp_memprobe) on `stream` (default: torch's current)."""
+    check(lib().spmttkrp_memprobe(int(kind), ctypes.c_void_p(src.data_ptr()),
+                                  ctypes.c_void_p(dst.data_ptr()), int(n), int(run),
+                                  _stream_ptr(stream)))
 
 
 def check_elements(elems, nnz: int, dims, elem_bytes: int, next_pos=None, alpha_word: int = 0,
@@ -280,15 +290,18 @@ class Plan:
                                 ctypes.byref(fit)))
         return fit.value
 
-    def loss_fwd(self, factors, loss):
-        """CP-loss forward; its residuals stay in the plan for the next loss_bwd.
-        Returns the plan's loss generation, which this call advances."""
+    def loss_fwd(self, factors, loss, forward_only: bool = False):
+        """CP-loss forward; its residuals (and, for fused plans, the gradient of the
+        current mode) stay in the plan for the next loss_bwd.  forward_only runs
+        the plain forward pass.  Returns the plan's loss generation, which this
+        call advances."""
         import torch
         self._check_factors(factors)
         if loss.dtype != torch.float32 or loss.numel() != 1:
             raise ValueError("loss: float32 scalar tensor")
         self._sync_stream()
-        check(lib().cp_loss_fwd(self._h, _ptrs(factors), ctypes.c_void_p(loss.data_ptr())))
+        check(lib().cp_loss_fwd_ex(self._h, _ptrs(factors), ctypes.c_void_p(loss.data_ptr()),
+                                   1 if forward_only else 0))
         self.loss_generation += 1
         return self.loss_generation
 
@@ -332,7 +345,9 @@ class Plan:
         d = dict(zip(keys, buf.tolist()))
         d["normx2"] = float(buf[14:15].view(np.float64)[0])
         flags = d["host_only"]
-        d["host_only"], d["variant"], d["keep_base"] = flags & 1, (flags >> 1) & 1, (flags >> 2) & 1
+        d["host_only"], d["variant"], d["keep_base"] = flags & 1, (flags >> 8) & 3, (flags >> 2) & 1
+        d["write_orders"] = (flags >> 10) & 1
+        d["hot_rows"] = (flags >> 11) & 0x1FFFFF
         d["stages"] = (flags >> 3) & 7
         d["partition"] = (flags >> 6) & 1
         d["remap_ids_in_elements"] = (flags >> 7) & 1

@@ -27,7 +27,8 @@ int launch_cp_fwd(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N
 
 // api.cu
 int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
-             const uint8_t* ein, uint8_t* eout, const float* scale);
+             const uint8_t* ein, uint8_t* eout, const float* scale,
+             double* loss_part = nullptr);
 int compute_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
                  bool keep_order);
 int upload_mode_tables(spmttkrp_plan* p, int n);

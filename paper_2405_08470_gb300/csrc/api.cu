@@ -149,8 +149,10 @@ static int remap_step(spmttkrp_plan* p) {
     return SPM_OK;
   }
   const int dst = next_buf(p);
-  int st = launch_remap_only(cur_elems(p), p->d_elem[dst], p->md[(size_t)m].next_pos, p->nnz,
-                             p->es, p->stream);
+  int st = p->worders
+               ? launch_remap_ordered(cur_elems(p), p->d_elem[dst], p->nnz, m, p->d_err, p->stream)
+               : launch_remap_only(cur_elems(p), p->d_elem[dst], p->md[(size_t)m].next_pos,
+                                   p->nnz, p->es, p->stream);
   if (st) return st;
   p->cur_buf = dst;
   p->cur_mode = (m + 1) % p->N;
@@ -173,7 +175,7 @@ static int check_device_word(spmttkrp_plan* p) {
 
 // Mode-n fused compute + remap on an explicit element copy pair.
 int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
-             const uint8_t* ein, uint8_t* eout, const float* scale) {
+             const uint8_t* ein, uint8_t* eout, const float* scale, double* loss_part) {
   if (p->nnz == 0) return launch_zero_rows(out, p->dims[(size_t)mode], p->R, p->stream);
   const ModeDev& d = p->md[(size_t)mode];
   MttkrpArgs a;
@@ -205,6 +207,10 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   a.stall_test = p->stall_test;
   a.nnz = p->nnz;
   a.grid_ctas = p->num_sms;
+  a.sched = p->d_err + 1;
+  a.hot_flags = p->hot_rows > 0 && (p->hints & 4);  // read by the tile form only
+  a.loss_part = loss_part;  // the fused CP-loss pass (always the warp-block form)
+  if (loss_part) a.variant = 0;
   if (a.variant == 2 && !p->worders) a.variant = 0;  // no write orders: form 0
   // the pass's elements carry their remap ids: word 4 + (next mode)
   a.alpha_word = p->alpha ? 4 + (mode + 1) % p->N : 0;
@@ -305,8 +311,8 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     return fail(SPM_ERR_INVALID_ARG, "unroll must be 0, 4 or 8");
   if (o.stages != 0 && (o.stages < 2 || o.stages > 4))
     return fail(SPM_ERR_INVALID_ARG, "stages must be 0 or in [2, 4]");
-  if (o.cache_hints < -1 || o.cache_hints > 3)
-    return fail(SPM_ERR_INVALID_ARG, "cache_hints must be in [-1, 3]");
+  if (o.cache_hints < -1 || o.cache_hints > 7)
+    return fail(SPM_ERR_INVALID_ARG, "cache_hints must be in [-1, 7]");
   if (o.keep_base != 0 && o.keep_base != 1)
     return fail(SPM_ERR_INVALID_ARG, "keep_base must be 0 or 1");
   if (o.wait_limit_ns < 0) return fail(SPM_ERR_INVALID_ARG, "wait_limit_ns must be >= 0");
@@ -389,9 +395,10 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     st = plan_dalloc(p, (void**)&p->d_elem[0], eb);
     if (!st) st = plan_dalloc(p, (void**)&p->d_elem[1], eb);
     if (!st && p->keep_base) st = plan_dalloc(p, (void**)&p->d_base, eb);
-    if (!st) st = plan_dalloc(p, (void**)&p->d_err, sizeof(int));
+    // d_err[0]: device error word; d_err[1]: the tile form's block counter
+    if (!st) st = plan_dalloc(p, (void**)&p->d_err, 4 * sizeof(int));
     if (!st) {
-      cudaError_t e = cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream);
+      cudaError_t e = cudaMemsetAsync(p->d_err, 0, 4 * sizeof(int), p->stream);
       if (e == cudaSuccess && eb && !device_orders)
         e = cudaMemcpyAsync(p->keep_base ? p->d_base : p->d_elem[0], p->h_elems.data(), eb,
                             cudaMemcpyHostToDevice, p->stream);
@@ -424,6 +431,7 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
     // the tile form's write orders (3 modes, nonzeros carrying remap ids)
     if (!st && p->alpha)
       st = build_write_orders(p, p->keep_base ? p->d_base : p->d_elem[0]);
+    if (!st && p->alpha) st = build_hot_flags(p, p->keep_base ? p->d_base : p->d_elem[0]);
     for (int n = 0; n < N && !st; ++n) st = upload_mode_tables(p, n);
     if (!st) {
       cudaError_t e = cudaStreamSynchronize(p->stream);
@@ -467,6 +475,8 @@ int spmttkrp_plan_destroy(spmttkrp_plan_t p) {
   dfree(p->d_chol);
   dfree(p->d_scal);
   dfree(p->d_vinv);
+  dfree(p->d_lossgrad);
+  dfree(p->d_lpart);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   p->destroyed = true;
   delete p;
@@ -619,8 +629,11 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
       o[13] = p->num_sms;
       std::memcpy(&o[14], &p->normx2, 8);
       o[15] = lane_config(p->R, p->dtype, true).L;
-      o[12] = p->host_only | (p->variant << 1) | (p->keep_base << 2) | (p->stages << 3) |
-              (p->partition << 6) | (p->alpha << 7);
+      o[12] = (int64_t)p->host_only | ((int64_t)(p->variant & 1) << 1) |
+              ((int64_t)p->keep_base << 2) | ((int64_t)p->stages << 3) |
+              ((int64_t)p->partition << 6) | ((int64_t)p->alpha << 7) |
+              ((int64_t)p->variant << 8) | ((int64_t)p->worders << 10) |
+              ((int64_t)p->hot_rows << 11);
       return SPM_OK;
     }
     case SPM_Q_NEXT_POS: {

@@ -231,16 +231,53 @@ int cp_als_iter(spmttkrp_plan_t p, void* const* factors, float* lambda, double* 
   return SPM_OK;
 }
 
-int cp_loss_fwd(spmttkrp_plan_t p, const void* const* factors, float* loss) {
+// The fused CP-loss pass serves plans whose nonzeros are 3-mode 32-byte sectors
+// and whose factors take the vector lanes (16-byte aligned, R a multiple of 4).
+static bool loss_fusable(const spmttkrp_plan* p, const void* const* factors) {
+  if (!(p->N == 3 && p->es == 32 && p->partition == 0 && p->nnz > 0)) return false;
+  bool al = true;
+  for (int k = 0; k < p->N; ++k) al = al && (((uintptr_t)factors[k] & 15u) == 0);
+  return lane_config(p->R, p->dtype, al, true).vec;
+}
+
+int cp_loss_fwd_ex(spmttkrp_plan_t p, const void* const* factors, float* loss, int flags) {
   NvtxRange range("cp_loss_fwd");
   if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
   if (p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
   if (!factors || !loss) return fail(SPM_ERR_INVALID_ARG, "null argument");
+  if (flags & ~SPM_LOSS_FORWARD_ONLY) return fail(SPM_ERR_INVALID_ARG, "unknown cp_loss flag");
   for (int k = 0; k < p->N; ++k)
     if (!factors[k]) return fail(SPM_ERR_INVALID_ARG, "null factor pointer");
   int st = ensure_als(p);
   if (st) return st;
   if ((st = ensure(p, (void**)&p->d_elem[2], (size_t)p->nnz * p->es))) return st;
+  p->res_valid = 0;
+  p->res_grad = -1;
+  const int n0 = p->cur_mode;
+  if (!(flags & SPM_LOSS_FORWARD_ONLY) && loss_fusable(p, factors)) {
+    // one pass: residuals, the mode-n0 gradient of L, the residual copy in the
+    // next mode's order, and per-block partial sums of e^2
+    if ((st = ensure(p, (void**)&p->d_lossgrad, (size_t)max_dim(p) * p->R * 4))) return st;
+    const size_t need = (size_t)std::max(1, p->md[(size_t)n0].nblk);
+    if (need > p->lpart_cap) {
+      if (p->d_lpart) {
+        cudaFree(p->d_lpart);
+        p->dev_bytes -= std::max<size_t>(p->lpart_cap * 8, 16);
+        p->d_lpart = nullptr;
+      }
+      if ((st = plan_dalloc(p, (void**)&p->d_lpart, need * 8))) return st;
+      p->lpart_cap = need;
+    }
+    st = run_mode(p, n0, factors, p->d_lossgrad, cur_elems(p), p->d_elem[2], nullptr,
+                  p->d_lpart);
+    if (st) return st;
+    st = launch_loss_reduce(p->d_lpart, p->md[(size_t)n0].nblk, loss, p->d_scal + 2, p->stream);
+    if (st) return st;
+    p->res_valid = 1;
+    p->res_mode = (n0 + 1) % p->N;
+    p->res_grad = n0;
+    return p->checks ? spmttkrp_device_status(p) : SPM_OK;
+  }
   FactorPtrs fp;
   for (int k = 0; k < p->N; ++k) fp.p[k] = factors[k];
   st = launch_cp_fwd(cur_elems(p), p->d_elem[2], p->nnz, p->es, p->N, fp, p->R,
@@ -249,6 +286,10 @@ int cp_loss_fwd(spmttkrp_plan_t p, const void* const* factors, float* loss) {
   p->res_valid = 1;
   p->res_mode = p->cur_mode;
   return SPM_OK;
+}
+
+int cp_loss_fwd(spmttkrp_plan_t p, const void* const* factors, float* loss) {
+  return cp_loss_fwd_ex(p, factors, loss, 0);
 }
 
 int cp_loss_bwd(spmttkrp_plan_t p, const void* const* factors, const float* grad_out,
@@ -265,15 +306,23 @@ int cp_loss_bwd(spmttkrp_plan_t p, const void* const* factors, const float* grad
   // is the working copy); it is dropped afterwards, so the last pass writes no
   // remap
   uint8_t* bufs[2] = {p->d_elem[2], p->d_elem[1 - p->cur_buf]};
-  int cur = 0;
-  for (int i = 0; i < p->N; ++i) {
-    const int n = (p->res_mode + i) % p->N;
+  int cur = 0, first = 0;
+  if (p->res_grad >= 0) {  // the fused forward's mode: its gradient, scaled
+    const int g = p->res_grad;
+    int st = launch_scale_copy(p->d_lossgrad, grads[g], p->dims[(size_t)g] * p->R, grad_out,
+                               p->stream);
+    if (st) return st;
+    first = 1;
+  }
+  for (int i = first; i < p->N; ++i) {
+    const int n = (p->res_mode + i - first) % p->N;
     int st = run_mode(p, n, factors, grads[n], bufs[cur], i == p->N - 1 ? nullptr : bufs[1 - cur],
                       grad_out);
     if (st) return st;
     if (p->nnz > 0) cur ^= 1;
   }
   p->res_valid = 0;
+  p->res_grad = -1;
   return p->checks ? spmttkrp_device_status(p) : SPM_OK;
 }
 

@@ -47,7 +47,7 @@ __global__ void check_elements_kernel(const uint8_t* __restrict__ elems, int64_t
       atomicMin(&st->first_target, (unsigned long long)q);
     } else {
       atomicAdd(&hits[t], 1u);
-      if (alpha_word > 0 && el[alpha_word] != t) {
+      if (alpha_word > 0 && (el[alpha_word] & 0x7fffffff) != t) {  // bit 31: hot-row flag
         atomicAdd(&st->bad_alpha, 1ull);
         atomicMin(&st->first_alpha, (unsigned long long)q);
       }

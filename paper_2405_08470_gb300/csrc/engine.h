@@ -106,6 +106,7 @@ struct spmttkrp_plan {
   int alpha = 0;  // stored nonzeros carry their remap ids: words 4..6 = position in
                   // the mode-0/1/2 order (3 modes in 32-byte sectors)
   int worders = 0;  // word 7 holds the write orders of the tile form (form 2)
+  int hot_rows = 0;   // rows per factor marked hot (bit 31 of words 4..6); 0 = none
   int lpt_kappa = 0;                               // partition 1: blocks per mode
   std::vector<std::vector<int64_t>> lpt_load;      // partition 1: nonzeros per block
   std::vector<std::vector<int32_t>> lpt_empty;     // partition 1: rows with no nonzero
@@ -113,7 +114,7 @@ struct spmttkrp_plan {
   std::vector<spm::ModeDev> md;
   float* d_part = nullptr;   // split-row partials: max nblk x 2 x R
   size_t part_cap = 0;       // floats
-  int* d_err = nullptr;      // device error word
+  int* d_err = nullptr;      // device error word [0] and the tile form's block counter [1]
   // ALS / CP-loss scratch (allocated on first use)
   float* d_M = nullptr;       // max_n dims[n] x R: spMTTKRP output of the ALS mode
   float* d_U = nullptr;       // max_n dims[n] x R: M V^-1 before normalisation
@@ -126,6 +127,10 @@ struct spmttkrp_plan {
   float* d_vinv = nullptr;    // R x R
   int res_valid = 0;          // residual copy d_elem[2] is current (after cp_loss_fwd)
   int res_mode = 0;           // order the residual copy is in
+  int res_grad = -1;          // >= 0: the fused forward left that mode's gradient in d_lossgrad
+  float* d_lossgrad = nullptr;  // max_n dims[n] x R: gradient of the fused forward's mode
+  double* d_lpart = nullptr;    // per-block partials of sum e^2 (fused forward)
+  size_t lpart_cap = 0;
   std::vector<spm::GraphCache> sweep_graphs;  // by parity
   std::vector<spm::GraphCache> als_graphs;
   bool destroyed = false;
@@ -171,6 +176,10 @@ int build_device_orders(spmttkrp_plan* p, const std::vector<std::vector<int32_t>
 // in word 7 of the nonzero occupying each slot.  `elems` is the copy in mode-0
 // order.
 int build_write_orders(spmttkrp_plan* p, uint8_t* elems);
+// Hot-row flags (3 modes, 32-byte nonzeros carrying remap ids): for every mode k,
+// the hot_rows rows of largest degree (ties to the lower row id); bit 31 of word
+// 4 + k of each nonzero (copy in mode-0 order) is set when its i_k is one of them.
+int build_hot_flags(spmttkrp_plan* p, uint8_t* elems);
 int default_tile(int es);
 int partition_mode(const spmttkrp_plan* p, int n, int nblk, ModeHost* out);
 int default_nblk(int64_t nnz, int num_sms, int variant);
@@ -192,7 +201,9 @@ struct MttkrpArgs {
   const float* scale;      // device scalar multiplier or null
   int dtype;
   int variant;             // 0 = warp blocks, staged tiles; 1 = CTA blocks, direct runs
-  int hints;               // bit0: streams evict_first in L2; bit1: factor rows evict_last
+  int hints;               // bit0: streams evict_first in L2; bit1: factor rows evict_last;
+                           // bit2: L1 choice by the hot-row flags (hot rows evict_last,
+                           // others evict_first)
   int unroll;              // nonzeros in flight per lane group (4 or 8; 0 = default)
   int stages;              // tiles per warp ring of the staged form (2..4)
   int no_fill;             // 1: blocks own non-contiguous row sets (Algorithm 1), so
@@ -207,6 +218,11 @@ struct MttkrpArgs {
                            // nothing completes, so it gives up after wait_ns
   int64_t nnz;             // nonzeros of the working copy (form 2 stages whole tiles)
   int grid_ctas;           // form 2: persistent CTAs (0 = one per block)
+  int* sched;              // form 2: device block counter (zeroed by the launcher)
+  double* loss_part;       // fused CP-loss pass: one FP64 partial of sum e^2 per block
+                           // (non-null selects the fused pass: see mttkrp_warp_kernel)
+  int hot_flags;           // bit 31 of word 4 + k of a stored nonzero marks i_k as one
+                           // of the hot rows of factor k (3 modes, 32-byte nonzeros)
 };
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s);
 // the tile form (form 2) covers 3 modes, 32-byte nonzeros carrying remap ids, R 16/32/64
@@ -218,6 +234,13 @@ int launch_zero_rows(float* out, int64_t rows, int R, cudaStream_t s);
 int launch_zero_listed_rows(float* out, const int32_t* rows, int nrows, int R, cudaStream_t s);
 int launch_remap_only(const uint8_t* in, uint8_t* out, const int32_t* next_pos, int64_t nnz,
                       int es, cudaStream_t s);
+int launch_scale_copy(const float* src, float* dst, int64_t n, const float* scale,
+                      cudaStream_t s);
+int launch_loss_reduce(const double* part, int64_t n, float* loss, double* loss64,
+                       cudaStream_t s);
+// remap-only pass in destination order (plans with write orders): mode -> mode+1
+int launch_remap_ordered(const uint8_t* in, uint8_t* out, int64_t nnz, int mode, int* err,
+                         cudaStream_t s);
 size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype, int stages);
 
 // The copy of the nonzeros in the working order (the resident mode-0 copy

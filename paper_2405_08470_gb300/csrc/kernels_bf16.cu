@@ -26,7 +26,44 @@ static int launch_direct_bfloat16(const MttkrpArgs& a, const LaneCfg& c, cudaStr
 }
 
 int launch_mttkrp_bf16(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
+  if (a.loss_part) {  // fused CP-loss pass (3 modes, 32-byte nonzeros, vector lanes)
+    if (!(c.vec && a.nmodes == 3 && a.es == 32))
+      return fail(SPM_ERR_UNSUPPORTED, "fused CP-loss pass: 3 modes, 32-byte nonzeros only");
+    if (c.VW == 4) {
+      switch (a.mode) {
+        case 0: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 4, 0, 32, true>(a, c.L, s);
+        case 1: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 4, 1, 32, true>(a, c.L, s);
+        default: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 4, 2, 32, true>(a, c.L, s);
+      }
+    }
+    switch (a.mode) {
+      case 0: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 0, 32, true>(a, c.L, s);
+      case 1: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 1, 32, true>(a, c.L, s);
+      default: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 2, 32, true>(a, c.L, s);
+    }
+  }
   if (a.variant == 1) return launch_direct_bfloat16(a, c, s);
+  if (c.vec && c.VW == 4) {  // 8-byte lane slices (R <= 32): the FP32 kernel's lane shape
+    switch (a.nmodes) {
+      case 3:
+        if (a.es == 32) {
+          switch (a.mode) {
+            case 0: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 8, 0, 32>(a, c.L, s);
+            case 1: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 8, 1, 32>(a, c.L, s);
+            default: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 8, 2, 32>(a, c.L, s);
+          }
+        }
+        switch (a.mode) {
+          case 0: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 8, 0>(a, c.L, s);
+          case 1: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 8, 1>(a, c.L, s);
+          default: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 8, 2>(a, c.L, s);
+        }
+      case 4: return launch_warp_kernel<4, __nv_bfloat16, 4, 1, 4>(a, c.L, s);
+      case 5: return launch_warp_kernel<5, __nv_bfloat16, 4, 1, 4>(a, c.L, s);
+      case 6: return launch_warp_kernel<6, __nv_bfloat16, 4, 1, 4>(a, c.L, s);
+      default: return launch_warp_kernel<0, __nv_bfloat16, 4, 1, 4>(a, c.L, s);
+    }
+  }
   if (c.vec) {
     switch (a.nmodes) {
       case 3:

@@ -1,6 +1,7 @@
 // kernels_misc.cu - split-row fix-up, zero fill, remap-only pass, and the
 // dispatcher of the fused spMTTKRP + remap kernel.
 #include "mttkrp_kernel.cuh"
+#include "mttkrp_tile.cuh"
 
 namespace spm {
 
@@ -14,13 +15,13 @@ static LaneCfg cfg_for(const MttkrpArgs& a) {
   bool al = aligned16(a.out);
   for (int k = 0; k < a.nmodes; ++k)
     if (k != a.mode) al = al && aligned16(a.factors[k]);
-  return lane_config(a.R, a.dtype, al);
+  return lane_config(a.R, a.dtype, al, a.variant == 0);
 }
 
 size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype, int stages) {
   size_t m = 0;
   for (bool al : {true, false}) {
-    const LaneCfg c = lane_config(R, dtype, al);
+    const LaneCfg c = lane_config(R, dtype, al, true);
     const int G = 32 / c.L;
     m = std::max(m, (size_t)kWarps * warp_layout(es, warp_tile_for(tile, G), R, G, stages).total);
   }
@@ -30,6 +31,8 @@ size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype, int stages) {
 int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s) {
   if (a.nblk <= 0) return SPM_OK;
   LaneCfg c = cfg_for(a);
+  if (a.loss_part)  // the fused CP-loss pass runs in the warp-block form
+    return a.dtype == SPM_DTYPE_BF16 ? launch_mttkrp_bf16(a, c, s) : launch_mttkrp_f32(a, c, s);
   if (a.variant == 2) {
     // the tile form needs 16-byte aligned factors and output; otherwise form 0
     bool al = aligned16(a.out);
@@ -181,6 +184,90 @@ __global__ void remap_only_kernel(const uint4* __restrict__ in, uint4* __restric
   const int64_t p = nv == 1 ? i : i / nv;
   const int c = (int)(i - p * nv);
   out[(int64_t)__ldg(next_pos + p) * nv + c] = __ldg(in + i);
+}
+
+// dst = scale * src over n floats (the CP-loss gradient of the fused pass's mode).
+__global__ void scale_copy_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                  int64_t n, const float* __restrict__ scale) {
+  const float sc = scale ? __ldg(scale) : 1.0f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    dst[i] = __ldg(src + i) * sc;
+}
+
+int launch_scale_copy(const float* src, float* dst, int64_t n, const float* scale,
+                      cudaStream_t s) {
+  if (n <= 0) return SPM_OK;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+  scale_copy_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, n, scale);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "scale_copy_kernel launch");
+}
+
+// 1/2 sum of n FP64 partials in a fixed order: thread t adds a contiguous chunk,
+// then the 256 chunk sums are added in a fixed tree; loss = that half-sum.
+__global__ void __launch_bounds__(256) loss_reduce_kernel(const double* __restrict__ part,
+                                                          int64_t n, float* __restrict__ loss,
+                                                          double* __restrict__ loss64) {
+  __shared__ double red[256];
+  const int64_t chunk = (n + 255) / 256;
+  const int64_t b = (int64_t)threadIdx.x * chunk, e = min(n, b + chunk);
+  double acc = 0.0;
+  for (int64_t i = b; i < e; ++i) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    loss64[0] = 0.5 * red[0];
+    loss[0] = (float)(0.5 * red[0]);
+  }
+}
+
+int launch_loss_reduce(const double* part, int64_t n, float* loss, double* loss64,
+                       cudaStream_t s) {
+  loss_reduce_kernel<<<1, 256, 0, s>>>(part, n, loss, loss64);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "loss_reduce_kernel launch");
+}
+
+// Remap-only pass in destination order, for 3-mode nonzeros in 32-byte sectors
+// that carry their remap ids and write orders: thread j takes slot j of its
+// tile of kTileNnz positions, reads there the tile-local index of the nonzero
+// whose destination is the tile's j-th smallest, and stores that nonzero.
+// Consecutive threads then store consecutive sectors wherever destinations are
+// consecutive (the stable partition of Observation 1).
+__global__ void remap_ordered_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+                                     int64_t nnz, int mode, int* err) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nnz) return;
+  const int64_t base = j - j % kTileNnz;
+  const uint32_t wo = __ldg(reinterpret_cast<const uint32_t*>(in + j * 32) + kTileWordW);
+  const int64_t src = base + ((wo >> (10 * mode)) & 1023u);
+  if (src >= nnz) {
+    if (err) atomicOr(err, 2);
+    return;
+  }
+  const uint4* sp = reinterpret_cast<const uint4*>(in + src * 32);
+  const uint4 lo = __ldg(sp), hi = __ldg(sp + 1);
+  const int nx = (mode + 1) % 3;
+  const uint32_t dst = (nx == 0 ? hi.x : (nx == 1 ? hi.y : hi.z)) & kAlphaMask;
+  if ((int64_t)dst >= nnz) {
+    if (err) atomicOr(err, 2);
+    return;
+  }
+  st_hint_v8(out + (int64_t)dst * 32, lo, hi, make_policy(1));
+}
+
+int launch_remap_ordered(const uint8_t* in, uint8_t* out, int64_t nnz, int mode, int* err,
+                         cudaStream_t s) {
+  if (nnz <= 0) return SPM_OK;
+  const int64_t blocks = (nnz + 255) / 256;
+  remap_ordered_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, nnz, mode, err);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "remap_ordered_kernel launch");
 }
 
 int launch_remap_only(const uint8_t* in, uint8_t* out, const int32_t* next_pos, int64_t nnz,

@@ -20,17 +20,18 @@ bool tile_form_supported(int nmodes, int es, int alpha_word, int R) {
 }
 
 int launch_mttkrp_tile(const MttkrpArgs& a, cudaStream_t s) {
+  constexpr int U = kTileU, UH = kTileU / 2 > 0 ? kTileU / 2 : 1;
   if (a.dtype == SPM_DTYPE_BF16) {
     switch (a.R) {
-      case 16: return tile_by_mode<__nv_bfloat16, 2, 8>(a, s);
-      case 32: return tile_by_mode<__nv_bfloat16, 4, 8>(a, s);
-      default: return tile_by_mode<__nv_bfloat16, 8, 8>(a, s);
+      case 16: return tile_by_mode<__nv_bfloat16, 2, U>(a, s);
+      case 32: return tile_by_mode<__nv_bfloat16, 4, U>(a, s);
+      default: return tile_by_mode<__nv_bfloat16, 8, U>(a, s);
     }
   }
   switch (a.R) {
-    case 16: return tile_by_mode<float, 2, 8>(a, s);
-    case 32: return tile_by_mode<float, 4, 8>(a, s);
-    default: return tile_by_mode<float, 8, 4>(a, s);
+    case 16: return tile_by_mode<float, 2, U>(a, s);
+    case 32: return tile_by_mode<float, 4, U>(a, s);
+    default: return tile_by_mode<float, 8, UH>(a, s);
   }
 }
 

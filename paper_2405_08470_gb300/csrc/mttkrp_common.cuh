@@ -26,9 +26,11 @@ __host__ __device__ inline int pow2ceil(int x) {
   return p;
 }
 
-inline LaneCfg lane_config(int R, int dtype, bool aligned16) {
+// narrow_bf16: BF16 rows of R <= 32 values use 8-byte lane slices (4 values), so
+// that a rank-32 row takes 8 lanes, as an FP32 one does (the warp-block form).
+inline LaneCfg lane_config(int R, int dtype, bool aligned16, bool narrow_bf16 = false) {
   LaneCfg c;
-  int vw = dtype == SPM_DTYPE_BF16 ? 8 : 4;
+  int vw = dtype == SPM_DTYPE_BF16 ? ((narrow_bf16 && R <= 32) ? 4 : 8) : 4;
   if (aligned16 && R % vw == 0 && R / vw <= 32) {
     c.vec = true;
     c.VW = vw;
@@ -132,6 +134,43 @@ __device__ __forceinline__ uint4 ld_nc_hint_v4(const void* ptr, uint64_t policy)
   asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                : "l"(ptr), "l"(policy));
+  return v;
+}
+
+// 8-byte read-only global load with an L2 cache policy, and with an L1 choice.
+__device__ __forceinline__ uint2 ld_nc_hint_v2(const void* ptr, uint64_t policy) {
+  uint2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+               : "=r"(v.x), "=r"(v.y)
+               : "l"(ptr), "l"(policy));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_nc_l1_v2(const void* ptr, uint64_t policy, bool keep) {
+  uint2 v;
+  if (keep)
+    asm volatile("ld.global.nc.L1::evict_last.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(ptr), "l"(policy));
+  else
+    asm volatile("ld.global.nc.L1::evict_first.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(ptr), "l"(policy));
+  return v;
+}
+
+// 16-byte read-only global load with an L1 choice and an L2 cache policy: rows
+// marked hot are kept in L1 longest (evict_last), the others leave it first
+// (evict_first), so that L1 favours the most frequently gathered factor rows.
+__device__ __forceinline__ uint4 ld_nc_l1_v4(const void* ptr, uint64_t policy, bool keep) {
+  uint4 v;
+  if (keep)
+    asm volatile("ld.global.nc.L1::evict_last.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(ptr), "l"(policy));
+  else
+    asm volatile("ld.global.nc.L1::evict_first.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(ptr), "l"(policy));
   return v;
 }
 

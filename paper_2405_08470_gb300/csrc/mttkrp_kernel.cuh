@@ -100,6 +100,42 @@ struct Landing {
   }
 };
 
+// BF16 rows in 8-byte lane slices (4 values per lane)
+template <>
+struct Landing<__nv_bfloat16, 4, 1> {
+  using type = uint2;
+  __device__ __forceinline__ static void load(const void* base, int64_t row, int R, int sub,
+                                              int L, uint64_t pol, type& out) {
+    if (sub * 4 < R)
+      out = ld_nc_hint_v2(
+          reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(base) + row * R) + sub,
+          pol);
+    else
+      out = make_uint2(0u, 0u);
+  }
+  __device__ __forceinline__ static void unpack(const type& v, float* x) {
+    x[0] = __uint_as_float(v.x << 16);
+    x[1] = __uint_as_float(v.x & 0xffff0000u);
+    x[2] = __uint_as_float(v.y << 16);
+    x[3] = __uint_as_float(v.y & 0xffff0000u);
+  }
+};
+
+// One lane's slice of a factor row at ptr (16 or 8 bytes); with `flagged`, the L1
+// choice of a hot-row flag (keep: evict_last; else evict_first).
+template <typename LT>
+__device__ __forceinline__ LT load_lane(const uint8_t* ptr, uint64_t pol, bool flagged, bool keep);
+template <>
+__device__ __forceinline__ uint4 load_lane<uint4>(const uint8_t* ptr, uint64_t pol, bool flagged,
+                                                  bool keep) {
+  return flagged ? ld_nc_l1_v4(ptr, pol, keep) : ld_nc_hint_v4(ptr, pol);
+}
+template <>
+__device__ __forceinline__ uint2 load_lane<uint2>(const uint8_t* ptr, uint64_t pol, bool flagged,
+                                                  bool keep) {
+  return flagged ? ld_nc_l1_v2(ptr, pol, keep) : ld_nc_hint_v2(ptr, pol);
+}
+
 template <typename T, int RC>
 struct Landing<T, 1, RC> {
   struct type {
@@ -124,9 +160,17 @@ struct Landing<T, 1, RC> {
 // U: nonzeros in flight per lane group; MODE: output mode at compile time (3
 // modes only; -1 = runtime); ESB: element bytes when fixed (0 = the smallest
 // multiple of 16 that holds N indices and the value).
-template <int NT, typename T, int VW, int RC, int U, int MODE, int ESB = 0>
-__global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 : 2))
+// LOSS (3 modes, 32-byte nonzeros): the fused first pass of the CP loss.  Each
+// nonzero's own factor row A_n[i_n] is gathered as well; the model value
+// m_e = sum_r prod_k A_k[i_k, r] and the residual e = m_e - x_e replace the
+// value in the pass (so `out` receives the mode-n gradient of L = 1/2 sum e^2),
+// the remapped copy written is the residual copy (the value word holds e), and
+// every block leaves its FP64 partial of sum e^2 in loss_part.
+template <int NT, typename T, int VW, int RC, int U, int MODE, int ESB = 0, bool LOSS = false>
+__global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LOSS) ? 3 : 2))
     mttkrp_warp_kernel(const MttkrpArgs a, const int L) {
+  static_assert(!LOSS || (NT == 3 && MODE >= 0 && VW > 1 && ESB == 32),
+                "the fused CP-loss pass is built for 3 modes and 32-byte nonzeros");
   constexpr int NV = VW * RC;
   const int N = NT > 0 ? NT : a.nmodes;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -140,7 +184,10 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
   if (wb >= a.nblk) return;
   const int4 bi = a.blkinfo[wb];
   const int lo = bi.x, hi = bi.y;
-  if (lo >= hi) return;
+  if (lo >= hi) {
+    if (LOSS && lane == 0) a.loss_part[wb] = 0.0;
+    return;
+  }
 
   extern __shared__ __align__(128) uint8_t smem[];
   const int S = a.stages;
@@ -168,16 +215,24 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
   // once per mode (evict first); factor rows are reused (evict last)
   const uint64_t pol_stream = make_policy((a.hints & 1) ? 1 : 0);
   const uint64_t pol_factor = make_policy((a.hints & 2) ? 2 : 0);
-  // static 3-mode vector path: this lane's 16-byte slice of the two input
+  // static 3-mode vector path: this lane's slice (VW values) of the two input
   // factors' rows (lanes past R read slice 0; their values are never stored)
   const uint32_t rowb = (uint32_t)R * (uint32_t)sizeof(T);
+  constexpr int LB = VW * (int)sizeof(T);  // bytes of a lane's slice (16, or 8 for BF16 VW 4)
   const uint8_t* lane_base[2];
   {
     const int lsub = (sub * VW < R) ? sub : 0;
     const int k1 = (MODE >= 0 ? MODE : 0) + 1, k2 = (MODE >= 0 ? MODE : 0) + 2;
-    lane_base[0] = static_cast<const uint8_t*>(a.factors[k1 % 3 < N ? k1 % 3 : 0]) + lsub * 16;
-    lane_base[1] = static_cast<const uint8_t*>(a.factors[k2 % 3 < N ? k2 % 3 : 0]) + lsub * 16;
+    lane_base[0] = static_cast<const uint8_t*>(a.factors[k1 % 3 < N ? k1 % 3 : 0]) + lsub * LB;
+    lane_base[1] = static_cast<const uint8_t*>(a.factors[k2 % 3 < N ? k2 % 3 : 0]) + lsub * LB;
   }
+  // fused CP loss: this lane's slice of the output mode's own factor, and the
+  // lane's running sum of squared residuals (FP32 per batch, FP64 across)
+  const uint8_t* own_base = nullptr;
+  const bool lane_live = sub * VW < R;
+  double lsum = 0.0;
+  if constexpr (LOSS)
+    own_base = static_cast<const uint8_t*>(a.factors[MODE]) + (lane_live ? sub : 0) * LB;
 
   // the group's leader stages the group's segment of tile t (one mbarrier
   // arrival per group and tile, with the segment's byte count)
@@ -307,15 +362,25 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
       }
     }
     typename Landing<T, VW, RC>::type raw[U][NI];
+    typename Landing<T, VW, RC>::type rown[LOSS ? U : 1];  // A_n[i_n] slices (fused loss)
+    if constexpr (LOSS) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (u < nb)
+          rown[u] = load_lane<typename Landing<T, VW, RC>::type>(
+              own_base + (uint64_t)(uint32_t)rows[u] * rowb, pol_factor, false, false);
+    }
     if constexpr (NT == 3 && MODE >= 0 && VW > 1) {
       // static modes: one 32 x 32 -> 64-bit multiply per row address
 #pragma unroll
       for (int j = 0; j < 2; ++j)
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          if (u < nb)
-            raw[u][j] = ld_nc_hint_v4(lane_base[j] + (uint64_t)(uint32_t)ixs[u][j] * rowb,
-                                      pol_factor);
+          if (u < nb) {
+            using LT = typename Landing<T, VW, RC>::type;
+            raw[u][j] = load_lane<LT>(lane_base[j] + (uint64_t)(uint32_t)ixs[u][j] * rowb,
+                                      pol_factor, false, false);
+          }
     } else {
 #pragma unroll
       for (int j = 0; j < NI; ++j) {
@@ -327,6 +392,34 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
             if (u < nb) Landing<T, VW, RC>::load(Ak, ixs[u][j], R, sub, L, pol_factor, raw[u][j]);
         }
       }
+    }
+    if constexpr (LOSS) {
+      // the residual of each nonzero: m_e = sum over the lanes of the group of
+      // sum_q A_k1 A_k2 A_n, then e = m_e - x_e replaces the value
+      float sq = 0.f;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (u < nb) {
+          float p[NV], x[NV], y[NV];
+          Landing<T, VW, RC>::unpack(raw[u][0], p);
+          Landing<T, VW, RC>::unpack(raw[u][1], x);
+          Landing<T, VW, RC>::unpack(rown[u], y);
+          float m = 0.f;
+#pragma unroll
+          for (int q = 0; q < NV; ++q) m = fmaf(p[q] * x[q], y[q], m);
+          if (!lane_live) m = 0.f;
+          // the group's lanes run together (their segment lengths agree), other
+          // groups may be on another batch size: shuffle within the group only
+          const unsigned gmask = L >= 32 ? 0xffffffffu : (((1u << L) - 1u) << (gw * L));
+          for (int off = L / 2; off > 0; off >>= 1) m += __shfl_xor_sync(gmask, m, off);
+          const float r = m - vals[u];
+          vals[u] = r;
+          sq = fmaf(r, r, sq);
+          if (sub == 0)  // the residual copy: the staged nonzero's value becomes e
+            reinterpret_cast<float*>(const_cast<uint8_t*>(eb) + (size_t)(e + u) * es)[3] = r;
+        }
+      }
+      if (sub == 0) lsum += (double)sq;
     }
     // rows are sorted within a run: if the batch's last nonzero is still in the
     // current row, every nonzero of the batch is, and no per-nonzero check is needed
@@ -481,7 +574,7 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
     const int n = max(0, min(K, gb - seg));
     eb = ebuf + ((size_t)st * TW + (size_t)gw * K) * es;
 
-    if (remap) {  // Algorithm 3: every element to its place in the next mode's order
+    auto do_remap = [&]() {  // Algorithm 3: every element to its place in the next mode's order
       const int32_t* np = npbuf + (st * G + gw) * NPK + (seg & 3);
       if (es % 32 == 0) {  // whole 32-byte sectors per store (no read of the old sector)
         const int nv = es >= 32 ? es / 32 : 1;
@@ -492,7 +585,9 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
           const uint4 lo = src[0], hi = src[1];
           // with the ids in the nonzero (32-byte stride, one sector: c == 0) the id is
           // word aw of the sector, i.e. component aw - 4 of its upper half
-          const int dst = aw ? (int)(aw == 4 ? hi.x : (aw == 5 ? hi.y : hi.z)) : np[e];
+          // (bit 31 of the id words is a hot-row flag, not part of the id)
+          const int dst = aw ? (int)((aw == 4 ? hi.x : (aw == 5 ? hi.y : hi.z)) & 0x7fffffffu)
+                             : np[e];
           st_hint_v8(a.elems_out + (size_t)dst * es + 32 * c, lo, hi, pol_stream);
         }
       } else {
@@ -504,7 +599,8 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
                      pol_stream);
         }
       }
-    }
+    };
+    if (remap && !LOSS) do_remap();
 
     // Algorithm 2 over this group's segment [0, n) of the tile
     int e = 0;
@@ -514,6 +610,10 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
     } else {
       for (; e + U <= n; e += U) batch_generic(e, U);
       for (; e < n; ++e) batch_generic(e, 1);
+    }
+    if constexpr (LOSS) {  // the residual nonzeros, now in shared memory, to the next order
+      __syncwarp();
+      if (remap) do_remap();
     }
     __syncwarp();
   }
@@ -567,6 +667,10 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3) ? 3 :
     __syncwarp();
   }
   if (crow >= 0) emit(crow, cprev, emitted == 0, true);
+  if constexpr (LOSS) {  // fixed-order warp sum of the lanes' partials
+    for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
+    if (lane == 0) a.loss_part[wb] = lsum;
+  }
 }
 
 // Nonzeros per warp tile for a requested size: G runs of an odd length K, so
@@ -578,13 +682,13 @@ __host__ __device__ inline int warp_tile_for(int tile, int G) {
   return G * K;
 }
 
-template <int NT, typename T, int VW, int RC, int U, int MODE = -1, int ESB = 0>
+template <int NT, typename T, int VW, int RC, int U, int MODE = -1, int ESB = 0, bool LOSS = false>
 int launch_warp_kernel(const MttkrpArgs& a0, int L, cudaStream_t s) {
   const int G = 32 / L;
   MttkrpArgs a = a0;
   a.tile = warp_tile_for(a0.tile, G);
   const size_t smem = (size_t)kWarps * warp_layout(a.es, a.tile, a.R, G, a.stages).total;
-  auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U, MODE, ESB>;
+  auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U, MODE, ESB, LOSS>;
   int st = ensure_dyn_smem((const void*)kfn, smem, "cudaFuncSetAttribute(mttkrp_warp)");
   if (st) return st;
   const int grid = (a.nblk + kWarps - 1) / kWarps;

@@ -491,3 +491,54 @@ int build_write_orders(spmttkrp_plan* p, uint8_t* elems) {
 }
 
 }  // namespace spm
+
+// ---------------------------------------------------------------------------
+// Hot-row flags.
+namespace spm {
+namespace {
+
+__global__ void hot_flag_kernel(uint8_t* __restrict__ elems, int64_t n,
+                                const uint8_t* __restrict__ h0, const uint8_t* __restrict__ h1,
+                                const uint8_t* __restrict__ h2) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  uint32_t* e = reinterpret_cast<uint32_t*>(elems + q * 32);
+  const uint8_t* h[3] = {h0, h1, h2};
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    e[4 + k] = (e[4 + k] & kAlphaMask) | (h[k][e[k]] ? 0x80000000u : 0u);
+}
+
+}  // namespace
+
+int build_hot_flags(spmttkrp_plan* p, uint8_t* elems) {
+  if (!(p->N == 3 && p->es == 32 && p->alpha) || p->nnz <= 0) return SPM_OK;
+  // rows per factor: the two gathered factors' hot rows together fill about 48 KB
+  // of L1 (192 rows of 32 FP32 values)
+  const int s = p->dtype == SPM_DTYPE_BF16 ? 2 : 4;
+  const int H = std::max(16, 24576 / (p->R * s));
+  Scratch sc;
+  uint8_t* dh[3];
+  for (int k = 0; k < 3; ++k) {
+    const int64_t I = p->dims[(size_t)k];
+    const std::vector<int64_t>& us = p->row_start[(size_t)k];
+    const std::vector<int64_t>& ur = p->row_start[(size_t)3 + k];
+    std::vector<std::pair<int64_t, int64_t>> deg(ur.size());  // (-degree, row)
+    for (size_t u = 0; u < ur.size(); ++u) deg[u] = {-(us[u + 1] - us[u]), ur[u]};
+    const size_t take = std::min<size_t>((size_t)H, deg.size());
+    std::partial_sort(deg.begin(), deg.begin() + (std::ptrdiff_t)take, deg.end());
+    std::vector<uint8_t> hot((size_t)I, 0);
+    for (size_t u = 0; u < take; ++u) hot[(size_t)deg[u].second] = 1;
+    int st = sc.alloc(&dh[k], (size_t)I);
+    if (st) return st;
+    SPM_CUDA(cudaMemcpyAsync(dh[k], hot.data(), (size_t)I, cudaMemcpyHostToDevice, p->stream));
+  }
+  hot_flag_kernel<<<grid_for(p->nnz, 256), 256, 0, p->stream>>>(elems, p->nnz, dh[0], dh[1], dh[2]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "hot_flag_kernel launch");
+  SPM_CUDA(cudaStreamSynchronize(p->stream));
+  p->hot_rows = H;
+  return SPM_OK;
+}
+
+}  // namespace spm

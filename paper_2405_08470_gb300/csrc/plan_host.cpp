@@ -107,9 +107,9 @@ int default_nblk(int64_t nnz, int num_sms, int variant) {
     nb = std::max<int64_t>(std::min<int64_t>((int64_t)num_sms * 24 * 16, (nnz + 255) / 256),
                            (nnz + 4095) / 4096);
   } else if (variant == 2) {
-    // tile form: 4 blocks per persistent CTA (one CTA per SM), each at least
-    // a few tiles long
-    nb = std::min<int64_t>((int64_t)num_sms * 4, (nnz + 4095) / 4096);
+    // tile form: about 16 blocks per SM, taken dynamically by the persistent
+    // CTAs, each at least four 960-nonzero tiles long
+    nb = std::min<int64_t>((int64_t)num_sms * 16, (nnz + 3839) / 3840);
   } else {
     // CTA blocks: about 32K nonzeros each, at least 4 per SM while each keeps
     // >= 256 nonzeros

@@ -16,14 +16,17 @@ def captured():
 
 
 def test_traffic_only_for_the_captured_configuration():
+    """Committed traffic is scaled per nonzero from the small capture, and only for
+    the captured kernel sources and launch configuration."""
     d, e = captured()
     cfg = dict(e["config"])
-    nnz = cfg.pop("nnz")
+    nnz = 100_000_000
     if d["kernel_digest"] != bench.kernel_digest():
         assert bench.ncu_traffic("c2", 32, "f32", nnz, cfg) is None
         return
-    assert bench.ncu_traffic("c2", 32, "f32", nnz, cfg) == e["dram_bytes_per_launch_full"]
-    assert bench.ncu_traffic("c2", 32, "f32", nnz // 5, cfg) is None
+    per = e["dram_bytes_per_nonzero_per_launch"]
+    assert bench.ncu_traffic("c2", 32, "f32", nnz, cfg) == per * nnz
+    assert bench.ncu_traffic("c2", 32, "f32", nnz // 5, cfg) == per * (nnz // 5)
     for k in cfg:
         other = dict(cfg, **{k: cfg[k] + 1})
         assert bench.ncu_traffic("c2", 32, "f32", nnz, other) is None, k

@@ -219,3 +219,44 @@ def test_autotune_keeps_results_and_caches(tmp_path, monkeypatch):
     assert p2.info()["nblk"] == p.info()["nblk"]
     p.close()
     p2.close()
+
+
+@pytest.mark.parametrize("dtype,R", [("f32", 32), ("bf16", 32), ("f32", 64), ("bf16", 16)])
+def test_fused_and_plain_forward_give_the_same_loss_and_gradients(dtype, R):
+    """The fused forward (residuals, the current mode's gradient and the residual
+    copy in the next order, in one pass) against the plain forward followed by a
+    full backward sweep: equal loss and gradients within FP32 summation order,
+    both against the FP64 oracle, and the working copy untouched by either."""
+    dims = (300, 200, 120)
+    coo, _ = synth.make_coo(dims, 40_000, (1.1, 1.1, 1.1), seed=R + 5)
+    x = synth.make_planted_targets(coo, dims, 8, 0.1, seed=6)
+    c, xv = coo.numpy(), x.numpy()
+    F = synth.make_factors(dims, R, seed=7, scale=0.3)
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+    Fd = [f.to(tdt).cuda() for f in F]
+    Fq = [f.to(tdt).float().numpy().astype(np.float64) for f in F]
+    p = Plan(c, xv, dims, R, dtype=dtype, nblk=57)
+    want_loss, _ = O.cp_loss(c, xv, Fq)
+    G = O.cp_loss_grad(c, xv, dims, Fq)
+    idx0, _ = p.elements()
+    for start in range(3):  # the fused pass runs in the working copy's current mode
+        p.remap(start)
+        got = {}
+        for fo in (False, True):
+            loss = torch.empty((), device="cuda")
+            g = [torch.full((d, R), float("nan"), device="cuda") for d in dims]
+            p.loss_fwd(Fd, loss, forward_only=fo)
+            p.loss_bwd(Fd, torch.full((), 2.0, device="cuda"), g)
+            torch.cuda.synchronize()
+            assert abs(loss.item() - want_loss) <= 1e-5 * abs(want_loss), (start, fo)
+            for k in range(3):
+                err = O.relerr(g[k].cpu().numpy().astype(np.float64), 2.0 * G[k])
+                assert err <= 1e-5, (start, fo, k, err)
+            got[fo] = g
+        for k in range(3):
+            assert O.relerr(got[False][k].cpu().numpy().astype(np.float64),
+                            got[True][k].cpu().numpy().astype(np.float64)) <= 1e-5
+    p.remap(0)
+    idx1, _ = p.elements()
+    assert np.array_equal(idx0, idx1)
+    p.close()

@@ -44,6 +44,12 @@ def check_raw(p, coo, m):
     for k in range(3):
         want = O.tile_write_order(coo, k, TILE)[pos[k][order]]
         assert np.array_equal((w >> (10 * k)) & 1023, want), k
+    # bit 31 of word 4 + k: i_k is one of the hot rows of factor k
+    H = p.info()["hot_rows"]
+    assert H > 0
+    for k in range(3):
+        hot = np.isin(coo[order, k], O.hot_rows(coo, k, H))
+        assert np.array_equal(raw[:, 4 + k] < 0, hot), k
 
 
 def run(coo, vals, dims, R, dtype="f32", nblk=0, seed=3, check_words=True):

@@ -314,6 +314,38 @@ def test_tile_write_order_visits_destinations_in_increasing_order(tile):
                 assert all(x < y for x, y in zip(along, along[1:]))
 
 
+def test_cp_loss_grad_rows_equal_full_gradient_rows():
+    """The row-by-row CP-loss gradient equals the rows of the full gradient (itself
+    checked against central differences), for every mode and for empty rows."""
+    rng = np.random.default_rng(70)
+    coo, vals, dims = tiny_tensor(rng, 3, maxdim=6, density=0.5)
+    F = [rng.standard_normal((d, 4)) for d in dims]
+    G = O.cp_loss_grad(coo, vals, dims, F)
+    for n in range(3):
+        rows = list(range(dims[n]))
+        assert np.allclose(O.cp_loss_grad_rows(coo, vals, F, n, rows), G[n], rtol=1e-12,
+                           atol=1e-12)
+
+
+def test_hot_rows_are_the_most_frequent():
+    """No row outside the hot set holds more nonzeros than one inside it, equal
+    counts prefer the lower row id, and empty rows never count."""
+    rng = np.random.default_rng(11)
+    for trial in range(20):
+        coo, vals, dims = tiny_tensor(rng, 3, maxdim=7, density=0.4)
+        for k in range(3):
+            for H in (1, 2, 3, 50):
+                hot = set(O.hot_rows(coo, k, H).tolist())
+                deg = np.bincount(coo[:, k], minlength=dims[k])
+                nonempty = [r for r in range(dims[k]) if deg[r] > 0]
+                assert len(hot) == min(H, len(nonempty))
+                assert all(deg[r] > 0 for r in hot)
+                for r in hot:
+                    for s in nonempty:
+                        if s not in hot:
+                            assert deg[r] > deg[s] or (deg[r] == deg[s] and r < s)
+
+
 def test_flycoo_memory_formula():
     # Section 3.5.1: N log2|X| + sum log2 I_h + value bits
     assert O.flycoo_bits(2 ** 20, [2 ** 10] * 3) == pytest.approx(3 * 20 + 30 + 32)
