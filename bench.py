@@ -590,7 +590,7 @@ def c5_cp_loss(args, stream, reps):
     for dt in ("f32", "bf16"):
         tdt = torch.bfloat16 if dt == "bf16" else torch.float32
         p = Plan(coo_h, x_h, spec.dims, R, dtype=dt)
-        Fg = [f.to(tdt).requires_grad_(True) for f in F]
+        Fg = [f.detach().clone().to(tdt).requires_grad_(True) for f in F]
         scratch = [torch.empty(d, R, device="cuda") for d in spec.dims]
         p.autotune([f.detach() for f in Fg], scratch)
         del scratch

@@ -219,6 +219,26 @@ int spmttkrp_sweep(spmttkrp_plan_t plan, const void* const* factors, float* cons
 int cp_als_iter(spmttkrp_plan_t plan, void* const* factors, float* lambda, double* fit);
 
 /*
+ * Up to max_iters CP-ALS iterations (each as cp_als_iter) run as ONE graph
+ * launch, stopping on the device once the fit changes by less than tol between
+ * two iterations (the convergence check of the ALS loop, Section 2.1.4): a chain
+ * of conditional graph nodes, each holding one iteration and its check, which
+ * decides whether the next node runs.  No host synchronisation happens between
+ * iterations; the call synchronizes once at the end.  The graph is built on
+ * the first call and replayed by later calls with the same pointers,
+ * max_iters, tol and working-copy buffer.
+ *   factors   host array of nmodes device pointers, read and overwritten.
+ *   lambda    device, float [rank], written.
+ *   max_iters 1..256.   tol  >= 0 (0: always max_iters iterations).
+ *   fits      host, double [max_iters]: fit after each iteration that ran.
+ *   iters     host, receives the number of iterations that ran.
+ * Errors: NOT_SPD (the loop stops at the failing iteration), INVALID_ARG,
+ * STATE, CUDA.
+ */
+int cp_als_run(spmttkrp_plan_t plan, void* const* factors, float* lambda, int max_iters,
+               double tol, double* fits, int* iters);
+
+/*
  * CP loss on the observed entries: L = 1/2 sum_e (m_e - x_e)^2 with
  * m_e = sum_r prod_k A_k[i_k(e), r]; keeps the residuals m_e - x_e in the plan.
  *   factors  host array of nmodes device pointers.

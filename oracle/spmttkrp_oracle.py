@@ -353,6 +353,38 @@ def hot_rows(coo, k, H):
     return np.sort(np.asarray(order[:int(H)], dtype=np.int64))
 
 
+def index_bits(dim):
+    """Bits of a mode-k index: ceil(log2 I_k), at least 1 (Section 3.5.1)."""
+    b = 1
+    while (1 << b) < int(dim):
+        b += 1
+    return b
+
+
+def flycoo_pack(coo, vals, dims):
+    """Nonzeros (in the given order) packed into 16 bytes each: the N indices as
+    bit fields of index_bits(I_k) bits, index k starting at the sum of the widths
+    before it, in a 96-bit little-endian field (words 0..2), and the FP32 value
+    in word 3.  Section 3.5 stores a nonzero's indices with log2 I_h bits each.
+    Returns uint32 [nnz, 4]."""
+    coo = np.asarray(coo)
+    widths = [index_bits(d) for d in dims]
+    if sum(widths) > 96:
+        raise ValueError("indices need more than 96 bits")
+    out = np.zeros((coo.shape[0], 4), dtype=np.uint32)
+    vbits = np.asarray(vals, dtype=np.float32).view(np.uint32)
+    for e in range(coo.shape[0]):
+        field, off = 0, 0
+        for k, b in enumerate(widths):
+            field |= int(coo[e, k]) << off
+            off += b
+        out[e, 0] = field & 0xFFFFFFFF
+        out[e, 1] = (field >> 32) & 0xFFFFFFFF
+        out[e, 2] = (field >> 64) & 0xFFFFFFFF
+        out[e, 3] = vbits[e]
+    return out
+
+
 def flycoo_bits(nnz, dims, value_bits=32):
     """Bits per nonzero of the FLYCOO element (Section 3.5.1).
 

@@ -84,6 +84,8 @@ def lib():
     L.spmttkrp_compute_ex.argtypes = [P, ctypes.c_int, P, P, ctypes.c_int]
     L.spmttkrp_sweep.argtypes = [P, P, P, ctypes.c_int]
     L.cp_als_iter.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double)]
+    L.cp_als_run.argtypes = [P, P, P, ctypes.c_int, ctypes.c_double,
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     L.cp_loss_fwd.argtypes = [P, P, P]
     L.cp_loss_fwd_ex.argtypes = [P, P, P, ctypes.c_int]
     L.cp_loss_bwd.argtypes = [P, P, P, P]
@@ -289,6 +291,20 @@ class Plan:
         check(lib().cp_als_iter(self._h, _ptrs(factors), ctypes.c_void_p(lam.data_ptr()),
                                 ctypes.byref(fit)))
         return fit.value
+
+    def als_run(self, factors, lam, max_iters: int, tol: float = 0.0) -> list:
+        """Up to max_iters CP-ALS iterations in one graph launch, stopping on the
+        device when the fit changes by less than tol; returns the fits."""
+        import torch
+        self._check_factors(factors)
+        if lam.dtype != torch.float32 or lam.numel() != self.rank or not lam.is_contiguous():
+            raise ValueError("lambda: contiguous float32 tensor of rank elements")
+        self._sync_stream()
+        fits = (ctypes.c_double * int(max_iters))()
+        n = ctypes.c_int()
+        check(lib().cp_als_run(self._h, _ptrs(factors), ctypes.c_void_p(lam.data_ptr()),
+                               int(max_iters), float(tol), fits, ctypes.byref(n)))
+        return [fits[i] for i in range(n.value)]
 
     def loss_fwd(self, factors, loss, forward_only: bool = False):
         """CP-loss forward; its residuals (and, for fused plans, the gradient of the

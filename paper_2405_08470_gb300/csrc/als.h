@@ -22,8 +22,12 @@ int launch_als_scale(const float* U, const float* M, void* A, int dtype, const d
 int launch_als_fit(const double* grams, int N, int R, const double* lam64, const double* mdot,
                    int nb, double normx2, double* fit_out, const int* status, cudaStream_t s);
 int launch_cp_fwd(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N,
-                  const FactorPtrs& fp, int R, int dtype, double* part, int nb, float* loss,
-                  double* loss64, cudaStream_t s);
+                  const FactorPtrs& fp, const PackInfo& pk, int R, int dtype, double* part,
+                  int nb, float* loss, double* loss64, cudaStream_t s);
+
+int launch_als_converge(const double* fit, const int* status, double* fits, int* iters, int t,
+                        double tol, cudaGraphConditionalHandle next, int has_next,
+                        cudaStream_t s);
 
 // api.cu
 int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,

@@ -127,6 +127,38 @@ int upload_mode_tables(spmttkrp_plan* p, int n) {
   return SPM_OK;
 }
 
+// Index k of a packed nonzero from its words 0..2 (host side of pk_field).
+uint32_t host_field(const uint32_t* w, int off, int b) {
+  uint64_t x;
+  if (off < 32)
+    x = (((uint64_t)w[1] << 32) | w[0]) >> off;
+  else if (off < 64)
+    x = (((uint64_t)w[2] << 32) | w[1]) >> (off - 32);
+  else
+    x = (uint64_t)(w[2] >> (off - 64));
+  return (uint32_t)x & ((1u << b) - 1u);
+}
+
+// Packs the N indices of one nonzero into words 0..2 (bit fields of the plan's
+// widths) and the value into word 3.
+void pack_nonzero(const PackInfo& pk, int N, const int32_t* idx, float v, uint32_t* w) {
+  uint64_t lo = 0, hi = 0;  // bits 0..63 and 64..127 of the field
+  for (int k = 0; k < N; ++k) {
+    const uint64_t x = (uint32_t)idx[k];
+    const int off = pk.off[k];
+    if (off < 64) {
+      lo |= x << off;
+      if (off + pk.bits[k] > 64) hi |= x >> (64 - off);
+    } else {
+      hi |= x << (off - 64);
+    }
+  }
+  w[0] = (uint32_t)lo;
+  w[1] = (uint32_t)(lo >> 32);
+  w[2] = (uint32_t)hi;
+  std::memcpy(&w[3], &v, 4);
+}
+
 static int check_plan(spmttkrp_plan* p, bool need_device = true) {
   if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
   if (need_device && p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
@@ -208,6 +240,8 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   a.nnz = p->nnz;
   a.grid_ctas = p->num_sms;
   a.sched = p->d_err + 1;
+  a.pk = p->pack;
+  if (p->pack.packed && a.variant == 1) a.variant = 0;  // form 1 reads plain indices only
   a.hot_flags = p->hot_rows > 0 && (p->hints & 4);  // read by the tile form only
   a.loss_part = loss_part;  // the fused CP-loss pass (always the warp-block form)
   if (loss_part) a.variant = 0;
@@ -344,13 +378,28 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   const int es_min = ((4 * nmodes + 4) + 15) & ~15;
   p->es = es_min <= 32 ? 32 : es_min;
   if (o.element_bytes != 0) {
-    if ((o.element_bytes != 16 && o.element_bytes != 32) || o.element_bytes < es_min) {
+    // 16 bytes with 4 or more modes: the indices packed into bit fields (Section
+    // 3.5) of their exact widths, when they fit 96 bits
+    int packed_bits = 0;
+    for (int k = 0; k < nmodes; ++k) {
+      int b = 1;
+      while (b < 31 && (int64_t(1) << b) < dims[k]) ++b;
+      p->pack.off[k] = (uint8_t)std::min(packed_bits, 255);
+      p->pack.bits[k] = (uint8_t)b;
+      packed_bits += b;
+    }
+    const bool pack = o.element_bytes == 16 && nmodes >= 4 && packed_bits <= 96;
+    if ((o.element_bytes != 16 && o.element_bytes != 32) ||
+        (o.element_bytes < es_min && !pack)) {
       delete p;
       return fail(SPM_ERR_INVALID_ARG,
-                  "element_bytes must be 0, 16 (up to 3 modes) or 32 (up to 7 modes)");
+                  "element_bytes must be 0, 16 (up to 3 modes, or packed indices of at most "
+                  "96 bits) or 32 (up to 7 modes)");
     }
     p->es = o.element_bytes;
+    p->pack.packed = pack ? 1 : 0;
   }
+  p->pack.vword = p->pack.packed ? 3 : nmodes;
   // 3-mode nonzeros in 32-byte sectors carry their remap ids in the padding (the
   // element tuple of Section 3.5), so the fused pass reads no next_pos array
   p->alpha = (nmodes == 3 && p->es == 32) ? 1 : 0;
@@ -456,6 +505,8 @@ int spmttkrp_plan_destroy(spmttkrp_plan_t p) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
   for (auto& g : p->als_graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& g : p->als_run_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (int i = 0; i < 3; ++i) dfree(p->d_elem[i]);
   dfree(p->d_base);
   for (auto& d : p->md) {
@@ -476,6 +527,7 @@ int spmttkrp_plan_destroy(spmttkrp_plan_t p) {
   dfree(p->d_scal);
   dfree(p->d_vinv);
   dfree(p->d_lossgrad);
+  dfree(p->d_fits);
   dfree(p->d_lpart);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   p->destroyed = true;
@@ -683,10 +735,19 @@ int spmttkrp_plan_query(spmttkrp_plan_t p, int what, int mode, void* dst, size_t
       uint8_t* o = (uint8_t*)dst;
       for (int64_t q = 0; q < nnz; ++q) {
         const uint8_t* e = src + (size_t)q * p->es;
-        if (what == SPM_Q_ELEMS)
-          std::memcpy(o + (size_t)q * N * 4, e, (size_t)N * 4);
-        else
-          std::memcpy(o + (size_t)q * 4, e + (size_t)N * 4, 4);
+        if (what == SPM_Q_ELEMS) {
+          if (p->pack.packed) {  // bit fields of words 0..2
+            uint32_t w[3];
+            std::memcpy(w, e, 12);
+            int32_t* oi = reinterpret_cast<int32_t*>(o + (size_t)q * N * 4);
+            for (int k = 0; k < N; ++k) oi[k] = (int32_t)host_field(w, p->pack.off[k],
+                                                                    p->pack.bits[k]);
+          } else {
+            std::memcpy(o + (size_t)q * N * 4, e, (size_t)N * 4);
+          }
+        } else {
+          std::memcpy(o + (size_t)q * 4, e + (size_t)p->pack.vword * 4, 4);
+        }
       }
       return SPM_OK;
     }

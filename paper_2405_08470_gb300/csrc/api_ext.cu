@@ -17,6 +17,8 @@
 
 namespace spm {
 
+constexpr int kMaxAlsRun = 256;  // iterations one cp_als_run graph may hold
+
 // Row chunks of a Gram matrix (FP32 within a chunk, FP64 across chunks in a fixed
 // order): enough chunks to fill the GPU, at most 32 MB of partials.
 static int gram_chunks(int R) { return R <= 64 ? 1024 : (R <= 128 ? 256 : 64); }
@@ -240,6 +242,124 @@ static bool loss_fusable(const spmttkrp_plan* p, const void* const* factors) {
   return lane_config(p->R, p->dtype, al, true).vec;
 }
 
+int cp_als_run(spmttkrp_plan_t p, void* const* factors, float* lambda, int max_iters,
+               double tol, double* fits, int* iters) {
+  NvtxRange range("cp_als_run");
+  if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
+  if (p->host_only) return fail(SPM_ERR_STATE, "plan was built host-only");
+  if (!factors || !lambda || !fits || !iters) return fail(SPM_ERR_INVALID_ARG, "null argument");
+  if (max_iters < 1 || max_iters > kMaxAlsRun)
+    return fail(SPM_ERR_INVALID_ARG, "max_iters must be in [1, 256]");
+  if (!(tol >= 0.0)) return fail(SPM_ERR_INVALID_ARG, "tol must be >= 0");
+  for (int k = 0; k < p->N; ++k)
+    if (!factors[k]) return fail(SPM_ERR_INVALID_ARG, "null factor pointer");
+  if (p->nnz == 0) return fail(SPM_ERR_INVALID_ARG, "CP-ALS needs at least one nonzero");
+  int st = ensure_als(p);
+  if (st) return st;
+  if (max_iters + 1 > p->fits_cap) {
+    if (p->d_fits) {
+      cudaFree(p->d_fits);
+      p->dev_bytes -= std::max<size_t>((size_t)p->fits_cap * 8, 16);
+      p->d_fits = nullptr;
+    }
+    if ((st = plan_dalloc(p, (void**)&p->d_fits, (size_t)(kMaxAlsRun + 1) * 8))) return st;
+    p->fits_cap = kMaxAlsRun + 1;
+  }
+  st = spmttkrp_remap(p, 0);
+  if (st) return st;
+  int* d_iters = reinterpret_cast<int*>(p->d_fits + kMaxAlsRun);
+  int* status = reinterpret_cast<int*>(p->d_scal);
+  double tolbits;
+  std::memcpy(&tolbits, &tol, 8);
+  std::vector<const void*> key(factors, factors + p->N);
+  key.push_back(lambda);
+  key.push_back((const void*)(intptr_t)p->cur_buf);
+  key.push_back((const void*)(intptr_t)max_iters);
+  key.push_back(reinterpret_cast<const void*>(*reinterpret_cast<const intptr_t*>(&tolbits)));
+  GraphCache* hit = nullptr;
+  for (auto& g : p->als_run_graphs)
+    if (g.key == key) hit = &g;
+  const int buf0 = p->cur_buf;
+  if (!hit) {
+    // the loop as one graph: a chain of max_iters conditional nodes, node t
+    // holding iteration t and its convergence check, which decides whether
+    // node t+1 runs (an iteration of an odd number of modes moves the working
+    // copy to the other buffer, so each iteration is captured with its own
+    // buffer parity)
+    cudaGraph_t g = nullptr;
+    SPM_CUDA(cudaGraphCreate(&g, 0));
+    std::vector<cudaGraphConditionalHandle> h((size_t)max_iters);
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < max_iters && e == cudaSuccess; ++t)
+      e = cudaGraphConditionalHandleCreate(&h[(size_t)t], g, t == 0 ? 1u : 0u,
+                                           cudaGraphCondAssignDefault);
+    if (!p->cap_stream && e == cudaSuccess)
+      e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    cudaGraphNode_t prev = nullptr;
+    cudaStream_t user = p->stream;
+    for (int t = 0; t < max_iters && e == cudaSuccess && !st; ++t) {
+      alignas(cudaGraphNodeParams) unsigned char npb[sizeof(cudaGraphNodeParams)];
+      std::memset(npb, 0, sizeof(npb));  // reserved fields must be zero
+      cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npb);
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h[(size_t)t];
+      np.conditional.type = cudaGraphCondTypeIf;
+      np.conditional.size = 1;
+      cudaGraphNode_t node = nullptr;
+      e = cudaGraphAddNode(&node, g, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &np);
+      if (e != cudaSuccess) break;
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      p->stream = p->cap_stream;
+      e = cudaStreamBeginCaptureToGraph(p->stream, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        st = als_enqueue(p, factors, lambda);
+        if (!st)
+          st = launch_als_converge(p->d_scal + 1, status, p->d_fits, d_iters, t, tol,
+                                   t + 1 < max_iters ? h[(size_t)t + 1] : h[(size_t)t],
+                                   t + 1 < max_iters ? 1 : 0, p->stream);
+        cudaGraph_t cap = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(p->stream, &cap);
+        if (e == cudaSuccess) e = e2;
+      }
+      p->stream = user;
+      prev = node;
+    }
+    p->stream = user;
+    p->cur_buf = buf0;
+    p->cur_mode = 0;
+    if (st || e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return st ? st : cuda_fail(e, "CP-ALS loop graph");
+    }
+    GraphCache gc;
+    gc.key = key;
+    e = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(CP-ALS loop)");
+    if (p->als_run_graphs.size() >= 2) {
+      cudaGraphExecDestroy(p->als_run_graphs.front().exec);
+      p->als_run_graphs.erase(p->als_run_graphs.begin());
+    }
+    p->als_run_graphs.push_back(gc);
+    hit = &p->als_run_graphs.back();
+  }
+  SPM_CUDA(cudaMemsetAsync(d_iters, 0, sizeof(int), p->stream));
+  SPM_CUDA(cudaGraphLaunch(hit->exec, p->stream));
+  int n = 0, stat = 0;
+  SPM_CUDA(cudaMemcpyAsync(&n, d_iters, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  SPM_CUDA(cudaMemcpyAsync(&stat, status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  SPM_CUDA(cudaMemcpyAsync(fits, p->d_fits, (size_t)max_iters * 8, cudaMemcpyDeviceToHost,
+                           p->stream));
+  SPM_CUDA(cudaStreamSynchronize(p->stream));
+  *iters = n;
+  // each iteration of an odd number of modes flips the working-copy buffer
+  if (!p->keep_base && (p->N & 1) && (n & 1)) p->cur_buf = 1 - buf0;
+  p->cur_mode = 0;
+  if (stat) return fail(SPM_ERR_NOT_SPD, "Hadamard product of Gram matrices is not SPD");
+  return SPM_OK;
+}
+
 int cp_loss_fwd_ex(spmttkrp_plan_t p, const void* const* factors, float* loss, int flags) {
   NvtxRange range("cp_loss_fwd");
   if (!p || p->destroyed) return fail(SPM_ERR_INVALID_ARG, "null or destroyed plan");
@@ -280,7 +400,7 @@ int cp_loss_fwd_ex(spmttkrp_plan_t p, const void* const* factors, float* loss, i
   }
   FactorPtrs fp;
   for (int k = 0; k < p->N; ++k) fp.p[k] = factors[k];
-  st = launch_cp_fwd(cur_elems(p), p->d_elem[2], p->nnz, p->es, p->N, fp, p->R,
+  st = launch_cp_fwd(cur_elems(p), p->d_elem[2], p->nnz, p->es, p->N, fp, p->pack, p->R,
                      p->dtype, p->d_red, p->red_nb, loss, p->d_scal + 2, p->stream);
   if (st) return st;
   p->res_valid = 1;
@@ -366,6 +486,7 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
           cands.push_back({n, t, 0, sg});
   }
   for (int n : {4, 8, 16, 32}) {
+    if (p->pack.packed) break;  // form 1 reads plain indices only
     if ((int64_t)n * p->num_sms * 1024 > p->nnz && n > 4) continue;
     if (fixed_blocks && n > 4) continue;
     cands.push_back({n, p->tile, 1, p->stages});

@@ -12,6 +12,7 @@
 #include <string>
 
 #include "engine.h"
+#include "mttkrp_common.cuh"
 
 namespace spm {
 namespace {
@@ -29,13 +30,16 @@ struct Dims16 {
 
 __global__ void check_elements_kernel(const uint8_t* __restrict__ elems, int64_t nnz, int N,
                                       Dims16 dims, int es, const int32_t* __restrict__ next_pos,
-                                      int alpha_word, unsigned int* __restrict__ hits,
-                                      CheckState* st) {
+                                      int alpha_word, PackInfo pk,
+                                      unsigned int* __restrict__ hits, CheckState* st) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nnz) return;
   const int32_t* el = reinterpret_cast<const int32_t*>(elems + q * es);
   bool ok = true;
-  for (int k = 0; k < N; ++k) ok = ok && el[k] >= 0 && (int64_t)el[k] < dims.d[k];
+  for (int k = 0; k < N; ++k) {
+    const int ik = elem_index(elems + q * es, k, pk);
+    ok = ok && ik >= 0 && (int64_t)ik < dims.d[k];
+  }
   if (!ok) {
     atomicAdd(&st->bad_index, 1ull);
     atomicMin(&st->first_index, (unsigned long long)q);
@@ -66,7 +70,7 @@ __global__ void check_hits_kernel(const unsigned int* __restrict__ hits, int64_t
 }
 
 int run_check(const uint8_t* elems, int64_t nnz, int N, const int64_t* dims, int es,
-              const int32_t* next_pos, int alpha_word, cudaStream_t s) {
+              const int32_t* next_pos, int alpha_word, const PackInfo& pk, cudaStream_t s) {
   if (nnz <= 0) return SPM_OK;
   Dims16 d{};
   for (int k = 0; k < N; ++k) d.d[k] = dims[k];
@@ -79,8 +83,8 @@ int run_check(const uint8_t* elems, int64_t nnz, int N, const int64_t* dims, int
   if (e == cudaSuccess) e = cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     const unsigned grid = (unsigned)((nnz + 255) / 256);
-    check_elements_kernel<<<grid, 256, 0, s>>>(elems, nnz, N, d, es, next_pos, alpha_word, hits,
-                                                dst);
+    check_elements_kernel<<<grid, 256, 0, s>>>(elems, nnz, N, d, es, next_pos, alpha_word, pk,
+                                                hits, dst);
     if (next_pos) check_hits_kernel<<<grid, 256, 0, s>>>(hits, nnz, dst);
     e = cudaGetLastError();
   }
@@ -121,7 +125,7 @@ int spmttkrp_check_elements(const void* elems, int64_t nnz, int nmodes, const in
   if (alpha_word && (alpha_word <= nmodes || 4 * alpha_word >= elem_bytes))
     return fail(SPM_ERR_INVALID_ARG, "check: alpha_word outside the padding");
   return run_check(static_cast<const uint8_t*>(elems), nnz, nmodes, dims, elem_bytes, next_pos,
-                   alpha_word, static_cast<cudaStream_t>(stream));
+                   alpha_word, PackInfo(), static_cast<cudaStream_t>(stream));
 }
 
 int spmttkrp_plan_check(spmttkrp_plan_t p) {
@@ -130,7 +134,7 @@ int spmttkrp_plan_check(spmttkrp_plan_t p) {
   const int m = p->cur_mode;
   const int aw = p->alpha ? 4 + (m + 1) % p->N : 0;
   return run_check(cur_elems(p), p->nnz, p->N, p->dims.data(), p->es, p->md[(size_t)m].next_pos,
-                   aw, p->stream);
+                   aw, p->pack, p->stream);
 }
 
 }  // extern "C"

@@ -18,6 +18,17 @@ constexpr int kMaxModes = 16;
 constexpr int kMaxRank = 256;
 constexpr int kThreads = 256;  // threads per CTA of the fused kernel
 
+// Stored layout of a nonzero's indices: plain (N int32 words, the value in word
+// N) or packed (Section 3.5: index k in bits [off[k], off[k] + bits[k]) of the
+// 96-bit little-endian field in words 0..2, the value in word 3; 16 bytes for
+// up to 6 modes whose index widths sum to at most 96 bits).
+struct PackInfo {
+  int packed = 0;
+  int vword = 0;  // word of the FP32 value
+  uint8_t off[kMaxModes] = {};
+  uint8_t bits[kMaxModes] = {};
+};
+
 // Per-block descriptor of one mode's contiguous split (int4 on the device):
 //   x = first position, y = one past the last position,
 //   z = row of position x-1 (the row before the block; -1 for none),
@@ -107,6 +118,7 @@ struct spmttkrp_plan {
                   // the mode-0/1/2 order (3 modes in 32-byte sectors)
   int worders = 0;  // word 7 holds the write orders of the tile form (form 2)
   int hot_rows = 0;   // rows per factor marked hot (bit 31 of words 4..6); 0 = none
+  spm::PackInfo pack;  // index layout of the stored nonzeros (packed: 16 bytes, 4-6 modes)
   int lpt_kappa = 0;                               // partition 1: blocks per mode
   std::vector<std::vector<int64_t>> lpt_load;      // partition 1: nonzeros per block
   std::vector<std::vector<int32_t>> lpt_empty;     // partition 1: rows with no nonzero
@@ -133,6 +145,9 @@ struct spmttkrp_plan {
   size_t lpart_cap = 0;
   std::vector<spm::GraphCache> sweep_graphs;  // by parity
   std::vector<spm::GraphCache> als_graphs;
+  std::vector<spm::GraphCache> als_run_graphs;  // whole ALS loops (cp_als_run)
+  double* d_fits = nullptr;    // cp_als_run: fit of every iteration, then the count
+  int fits_cap = 0;
   bool destroyed = false;
 };
 
@@ -161,6 +176,10 @@ int cuda_fail(cudaError_t e, const char* what);
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
 // current device (once per kernel and device; thread-safe).
 int ensure_dyn_smem(const void* kernel, size_t bytes, const char* what);
+
+// packed nonzeros (PackInfo) on the host
+uint32_t host_field(const uint32_t* w, int off, int b);
+void pack_nonzero(const PackInfo& pk, int N, const int32_t* idx, float v, uint32_t* w);
 
 // ---- host planning (plan_host.cpp) ----
 int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int nblk_opt);
@@ -219,6 +238,7 @@ struct MttkrpArgs {
   int64_t nnz;             // nonzeros of the working copy (form 2 stages whole tiles)
   int grid_ctas;           // form 2: persistent CTAs (0 = one per block)
   int* sched;              // form 2: device block counter (zeroed by the launcher)
+  PackInfo pk;             // index layout of the stored nonzeros
   double* loss_part;       // fused CP-loss pass: one FP64 partial of sum e^2 per block
                            // (non-null selects the fused pass: see mttkrp_warp_kernel)
   int hot_flags;           // bit 31 of word 4 + k of a stored nonzero marks i_k as one

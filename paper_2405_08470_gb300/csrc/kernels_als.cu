@@ -490,3 +490,29 @@ int launch_als_fit(const double* grams, int N, int R, const double* lam64, const
 }
 
 }  // namespace spm
+
+namespace spm {
+
+// Convergence check of iteration t inside a CP-ALS graph: records the fit,
+// counts the iteration, and lets the next iteration's conditional node run only
+// while the fit still moves by tol or more (and no mode failed).
+__global__ void als_converge_kernel(const double* __restrict__ fit, const int* __restrict__ status,
+                                    double* __restrict__ fits, int* __restrict__ iters, int t,
+                                    double tol, cudaGraphConditionalHandle next, int has_next) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double f = fit[0];
+  fits[t] = f;
+  iters[0] = t + 1;
+  const bool stop = status[0] != 0 || (t > 0 && fabs(f - fits[t - 1]) < tol);
+  if (has_next) cudaGraphSetConditional(next, stop ? 0u : 1u);
+}
+
+int launch_als_converge(const double* fit, const int* status, double* fits, int* iters, int t,
+                        double tol, cudaGraphConditionalHandle next, int has_next,
+                        cudaStream_t s) {
+  als_converge_kernel<<<1, 32, 0, s>>>(fit, status, fits, iters, t, tol, next, has_next);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "als_converge_kernel");
+}
+
+}  // namespace spm

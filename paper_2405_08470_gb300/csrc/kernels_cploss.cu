@@ -16,7 +16,8 @@ namespace spm {
 template <int NT, typename T, int VW, int RC>
 __global__ void __launch_bounds__(256) cp_fwd_kernel(const uint8_t* __restrict__ elems,
                                                      uint8_t* __restrict__ res, int64_t nnz,
-                                                     int es, int nmodes, FactorPtrs fp, int R,
+                                                     int es, int nmodes, FactorPtrs fp,
+                                                     PackInfo pk, int R,
                                                      int L, double* __restrict__ loss_part) {
   constexpr int NV = VW * RC;
   const int N = NT > 0 ? NT : nmodes;
@@ -33,11 +34,12 @@ __global__ void __launch_bounds__(256) cp_fwd_kernel(const uint8_t* __restrict__
     const int64_t e = eb + gw;
     const bool active = e < nnz;
     const int* el = reinterpret_cast<const int*>(elems + (active ? e : 0) * es);
+    const uint8_t* ep = reinterpret_cast<const uint8_t*>(el);
     float p[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) p[j] = active ? 1.f : 0.f;
     for (int k = 0; k < N && active; ++k) {
-      const int64_t idx = __ldg(el + k);
+      const int64_t idx = elem_index(ep, k, pk);
       float x[NV];
       if constexpr (VW > 1) {
         if (sub * VW < R) {
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(256) cp_fwd_kernel(const uint8_t* __restrict__
     for (int j = 0; j < NV; ++j) m += p[j];
     for (int off = L / 2; off > 0; off >>= 1) m += __shfl_xor_sync(0xffffffffu, m, off);
     if (active && sub == 0) {
-      const float x = __int_as_float(__ldg(el + N));
+      const float x = elem_value(ep, N, pk);
       const float r = m - x;
       run = fmaf(r, r, run);
       const int nv = es / 16;
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(256) cp_fwd_kernel(const uint8_t* __restrict__
       uint4* dst = reinterpret_cast<uint4*>(res + e * es);
       for (int c = 0; c < nv; ++c) {
         uint4 v = __ldg(src + c);
-        const int word = N - 4 * c;  // value field: int index N of the element
+        const int word = (pk.packed ? 3 : N) - 4 * c;  // the value field's word
         if (word == 0) v.x = __float_as_uint(r);
         else if (word == 1) v.y = __float_as_uint(r);
         else if (word == 2) v.z = __float_as_uint(r);
@@ -112,7 +114,7 @@ template <int NT, typename T, int VW, int U>
 __global__ void __launch_bounds__(256, 4) cp_fwd_batched_kernel(const uint8_t* __restrict__ elems,
                                                              uint8_t* __restrict__ res,
                                                              int64_t nnz, int es, FactorPtrs fp,
-                                                             int R, int L,
+                                                             PackInfo pk, int R, int L,
                                                              double* __restrict__ loss_part) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int sub = lane % L, gw = lane / L, G = 32 / L;
@@ -140,7 +142,16 @@ __global__ void __launch_bounds__(256, 4) cp_fwd_batched_kernel(const uint8_t* _
       const int f[4] = {w0.x, w0.y, w0.z, w0.w};
 #pragma unroll
       for (int k = 0; k < NT; ++k) idx[u][k] = k < 4 ? f[k < 4 ? k : 0] : 0;
-      val[u] = NT < 4 ? __int_as_float(f[NT < 4 ? NT : 0]) : __int_as_float(__ldg(el + NT));
+      if (NT < 4)
+        val[u] = __int_as_float(f[NT < 4 ? NT : 0]);
+      else if (!pk.packed)  // (a packed nonzero has no word NT: 16 bytes)
+        val[u] = __int_as_float(__ldg(el + NT));
+      if (pk.packed) {  // bit fields in words 0..2, the value in word 3
+        const uint32_t pw[3] = {(uint32_t)w0.x, (uint32_t)w0.y, (uint32_t)w0.z};
+#pragma unroll
+        for (int k = 0; k < NT; ++k) idx[u][k] = (int)pk_field(pw, pk.off[k], pk.bits[k]);
+        val[u] = __int_as_float(w0.w);
+      }
     }
     uint4 raw[U][NT];
 #pragma unroll
@@ -196,7 +207,7 @@ __global__ void __launch_bounds__(256, 4) cp_fwd_batched_kernel(const uint8_t* _
       if (!on) continue;
       const int64_t e = base + (int64_t)gw * U + u;
       uint4 v = __ldg(reinterpret_cast<const uint4*>(elems + e * es) + c);
-      const int word = NT - 4 * c;
+      const int word = (pk.packed ? 3 : NT) - 4 * c;
       if (word == 0) v.x = __float_as_uint(ru);
       else if (word == 1) v.y = __float_as_uint(ru);
       else if (word == 2) v.z = __float_as_uint(ru);
@@ -238,8 +249,8 @@ static int resident_grid(K kernel, int cap) {
 
 template <typename T>
 static int fwd_dispatch(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N,
-                        const FactorPtrs& fp, int R, bool aligned, double* part, int cap,
-                        cudaStream_t s) {
+                        const FactorPtrs& fp, const PackInfo& pk, int R, bool aligned,
+                        double* part, int cap, cudaStream_t s) {
   const int dtype = std::is_same<T, float>::value ? SPM_DTYPE_F32 : SPM_DTYPE_BF16;
   const LaneCfg c = lane_config(R, dtype, aligned);
   constexpr int VWV = std::is_same<T, float>::value ? 4 : 8;
@@ -247,35 +258,36 @@ static int fwd_dispatch(const uint8_t* elems, uint8_t* res, int64_t nnz, int es,
   if (c.vec) {
     if (N == 3) {
       nb = resident_grid(cp_fwd_batched_kernel<3, T, VWV, 4>, cap);
-      cp_fwd_batched_kernel<3, T, VWV, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, fp, R, c.L,
+      cp_fwd_batched_kernel<3, T, VWV, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, fp, pk, R, c.L,
                                                              part);
     } else if (N == 4) {
       nb = resident_grid(cp_fwd_batched_kernel<4, T, VWV, 4>, cap);
-      cp_fwd_batched_kernel<4, T, VWV, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, fp, R, c.L,
+      cp_fwd_batched_kernel<4, T, VWV, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, fp, pk, R, c.L,
                                                              part);
     } else {
-      cp_fwd_kernel<0, T, VWV, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part);
+      cp_fwd_kernel<0, T, VWV, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, pk, R, c.L, part);
     }
   } else {
     switch (c.RC) {
-      case 1: cp_fwd_kernel<0, T, 1, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part); break;
-      case 2: cp_fwd_kernel<0, T, 1, 2><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part); break;
-      case 4: cp_fwd_kernel<0, T, 1, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part); break;
-      default: cp_fwd_kernel<0, T, 1, 8><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, R, c.L, part); break;
+      case 1: cp_fwd_kernel<0, T, 1, 1><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, pk, R, c.L, part); break;
+      case 2: cp_fwd_kernel<0, T, 1, 2><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, pk, R, c.L, part); break;
+      case 4: cp_fwd_kernel<0, T, 1, 4><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, pk, R, c.L, part); break;
+      default: cp_fwd_kernel<0, T, 1, 8><<<nb, 256, 0, s>>>(elems, res, nnz, es, N, fp, pk, R, c.L, part); break;
     }
   }
   return nb;
 }
 
 int launch_cp_fwd(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N,
-                  const FactorPtrs& fp, int R, int dtype, double* part, int nb, float* loss,
-                  double* loss64, cudaStream_t s) {
+                  const FactorPtrs& fp, const PackInfo& pk, int R, int dtype, double* part,
+                  int nb, float* loss, double* loss64, cudaStream_t s) {
   bool aligned = true;
   for (int k = 0; k < N; ++k) aligned = aligned && (((uintptr_t)fp.p[k] & 15u) == 0);
   const int used = dtype == SPM_DTYPE_BF16
-                       ? fwd_dispatch<__nv_bfloat16>(elems, res, nnz, es, N, fp, R, aligned, part,
-                                                     nb, s)
-                       : fwd_dispatch<float>(elems, res, nnz, es, N, fp, R, aligned, part, nb, s);
+                       ? fwd_dispatch<__nv_bfloat16>(elems, res, nnz, es, N, fp, pk, R, aligned,
+                                                     part, nb, s)
+                       : fwd_dispatch<float>(elems, res, nnz, es, N, fp, pk, R, aligned, part, nb,
+                                             s);
   cp_loss_final_kernel<<<1, 32, 0, s>>>(part, used, loss, loss64);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SPM_OK : cuda_fail(e, "cp_fwd kernels");

@@ -50,6 +50,27 @@ inline LaneCfg lane_config(int R, int dtype, bool aligned16, bool narrow_bf16 = 
   return c;
 }
 
+// ------------------------------------------------------------ stored nonzeros
+
+// Index k of a stored nonzeros (plain: word k; packed: its bit field).
+__device__ __forceinline__ uint32_t pk_field(const uint32_t* w, int off, int b) {
+  uint64_t x;
+  if (off < 32)
+    x = (((uint64_t)w[1] << 32) | w[0]) >> off;
+  else if (off < 64)
+    x = (((uint64_t)w[2] << 32) | w[1]) >> (off - 32);
+  else
+    x = (uint64_t)(w[2] >> (off - 64));
+  return (uint32_t)x & ((1u << b) - 1u);
+}
+__device__ __forceinline__ int elem_index(const uint8_t* ep, int k, const PackInfo& pk) {
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(ep);
+  return pk.packed ? (int)pk_field(w, pk.off[k], pk.bits[k]) : (int)w[k];
+}
+__device__ __forceinline__ float elem_value(const uint8_t* ep, int N, const PackInfo& pk) {
+  return reinterpret_cast<const float*>(ep)[pk.packed ? 3 : N];
+}
+
 // ------------------------------------------------------------ PTX helpers
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -176,8 +176,9 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int G = 32 / L, sub = lane % L, gw = lane / L;
   // element stride: a compile-time constant when the number of modes is
+  // (packed nonzeros of 4 or more modes are 16 bytes: the plan's stride)
   constexpr int ES_C = ESB > 0 ? ESB : (NT > 0 ? (((4 * NT + 4) + 15) & ~15) : 0);
-  const int es = NT > 0 ? ES_C : a.es;
+  const int es = (NT > 0 && !a.pk.packed) ? ES_C : a.es;
   const int R = a.R, mode = MODE >= 0 ? MODE : a.mode;
   const int TW = a.tile, K = TW / G, NPK = np_stage_ints(K);
   const int wb = blockIdx.x * kWarps + warp;
@@ -346,6 +347,19 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
           ixs[u][0] = f[(MODE + 1) % 3];
           ixs[u][1] = f[(MODE + 2) % 3];
           vals[u] = __int_as_float(v.w);
+        } else if (a.pk.packed) {  // 4-6 modes in 16 bytes (bit fields)
+          const uint4 w4 = *reinterpret_cast<const uint4*>(ep);
+          const uint32_t w[3] = {w4.x, w4.y, w4.z};
+          rows[u] = (int)pk_field(w, a.pk.off[mode], a.pk.bits[mode]);
+          vals[u] = __uint_as_float(w4.w);
+          int k = mode;
+#pragma unroll
+          for (int j = 0; j < NI; ++j) {
+            if (j < N - 1) {
+              k = (k + 1 == N) ? 0 : k + 1;
+              ixs[u][j] = (int)pk_field(w, a.pk.off[k], a.pk.bits[k]);
+            }
+          }
         } else {
           const int* el = reinterpret_cast<const int*>(ep);
           rows[u] = el[mode];
@@ -504,9 +518,9 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (u < nb) {
-        const int* el = reinterpret_cast<const int*>(eb + (size_t)(e + u) * es);
-        rows[u] = el[mode];
-        vals[u] = __int_as_float(el[N]);
+        const uint8_t* ep = eb + (size_t)(e + u) * es;
+        rows[u] = elem_index(ep, mode, a.pk);
+        vals[u] = elem_value(ep, N, a.pk);
 #pragma unroll
         for (int q = 0; q < NV; ++q) prod[u][q] = vals[u];
       }
@@ -519,8 +533,8 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
         if (u < nb) {
           typename Landing<T, VW, RC>::type raw;
           float x[NV];
-          Landing<T, VW, RC>::load(Ak, reinterpret_cast<const int*>(eb + (size_t)(e + u) * es)[k],
-                                   R, sub, L, pol_factor, raw);
+          Landing<T, VW, RC>::load(Ak, elem_index(eb + (size_t)(e + u) * es, k, a.pk), R, sub, L,
+                                   pol_factor, raw);
           Landing<T, VW, RC>::unpack(raw, x);
 #pragma unroll
           for (int q = 0; q < NV; ++q) prod[u][q] *= x[q];

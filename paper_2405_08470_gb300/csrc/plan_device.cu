@@ -195,13 +195,30 @@ __global__ void duplicate_kernel(const int32_t* __restrict__ keys, int64_t n, in
   atomicMin(first, (unsigned long long)q);
 }
 
-// The working copy in `perm` order: {int32 idx[N]; float val; zero padding}.
+// The working copy in `perm` order: {int32 idx[N]; float val; zero padding}, or
+// the packed 16-byte form (index bit fields in words 0..2, value in word 3).
 __global__ void fill_elems_kernel(const int32_t* __restrict__ keys, const float* __restrict__ vals,
                                   int64_t n, int N, const int32_t* __restrict__ perm,
-                                  uint8_t* __restrict__ out, int es) {
+                                  uint8_t* __restrict__ out, int es, PackInfo pk) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
   const int32_t x = perm[q];
+  if (pk.packed) {
+    uint64_t lo = 0, hi = 0;
+    for (int k = 0; k < N; ++k) {
+      const uint64_t v = (uint32_t)keys[(int64_t)k * n + x];
+      const int off = pk.off[k];
+      if (off < 64) {
+        lo |= v << off;
+        if (off + pk.bits[k] > 64) hi |= v >> (64 - off);
+      } else {
+        hi |= v << (off - 64);
+      }
+    }
+    *reinterpret_cast<uint4*>(out + q * es) =
+        make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, __float_as_uint(vals[x]));
+    return;
+  }
   uint4* d = reinterpret_cast<uint4*>(out + q * es);
   for (int v = 0; v < es / 16; ++v) {
     uint32_t w[4];
@@ -366,7 +383,8 @@ int build_device_orders(spmttkrp_plan* p, const std::vector<std::vector<int32_t>
   SPM_CUDA(cudaMemcpyAsync(&dup, d_dup, sizeof(dup), cudaMemcpyDeviceToHost, s));
   SPM_CUDA(cudaStreamSynchronize(s));
   if (dup != none) return fail(SPM_ERR_DUPLICATE, "duplicate coordinate in the COO input");
-  fill_elems_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_keys, d_vals, n, N, cur, elems, p->es);
+  fill_elems_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_keys, d_vals, n, N, cur, elems, p->es,
+                                                      p->pack);
   if (p->alpha) inverse_kernel<<<grid_for(n, 256), 256, 0, s>>>(cur, pos0, n);
 
   // per mode: row starts (to the host), the next order, next_pos (stays on the device)

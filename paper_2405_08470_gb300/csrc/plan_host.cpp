@@ -394,8 +394,14 @@ int build_host_plan(spmttkrp_plan* p, const int64_t* coo, const float* vals, int
     for (int64_t q = b; q < e; ++q) {
       int32_t x = cur[(size_t)q];
       int32_t* d = reinterpret_cast<int32_t*>(&p->h_elems[(size_t)q * es]);
-      for (int k = 0; k < N; ++k) d[k] = key[k][x];
-      std::memcpy(&d[N], &vals[x], 4);
+      if (p->pack.packed) {  // Section 3.5 bit fields, value in word 3
+        int32_t idx[kMaxModes];
+        for (int k = 0; k < N; ++k) idx[k] = key[k][x];
+        pack_nonzero(p->pack, N, idx, vals[x], reinterpret_cast<uint32_t*>(d));
+      } else {
+        for (int k = 0; k < N; ++k) d[k] = key[k][x];
+        std::memcpy(&d[N], &vals[x], 4);
+      }
     }
   });
 

@@ -125,8 +125,8 @@ def test_host_error_paths(case, status):
 
 
 @pytest.mark.parametrize("N,eb,want", [(2, 0, 32), (3, 0, 32), (3, 16, 16), (3, 32, 32),
-                                        (4, 0, 32), (7, 0, 32), (8, 0, 48), (4, 16, None),
-                                        (3, 24, None), (8, 32, None)])
+                                        (4, 0, 32), (7, 0, 32), (8, 0, 48), (4, 16, 16),
+                                        (6, 16, 16), (3, 24, None), (8, 32, None)])
 def test_element_stride_rules(N, eb, want):
     # default: one whole 32-byte sector per nonzero when N indices + value fit
     dims = (4,) * N
@@ -192,3 +192,30 @@ def test_binding_rejects_bad_tensors_before_the_c_abi():
     with pytest.raises(ValueError, match="expected 3 factors"):
         p.sweep(F[:2], F)
     p.close()
+
+
+def test_packed_nonzeros_match_the_oracle_packing_and_order():
+    """16-byte nonzeros with 4-6 modes hold the indices as bit fields of their
+    exact widths (Section 3.5; oracle.flycoo_pack) and the value in word 3; the
+    working copy, read back through the query, is the oracle's mode-0 order."""
+    for dims in [(1000, 200, 50, 30), (500, 50, 5, 100, 20), (200, 20, 9, 5, 10, 5)]:
+        N = len(dims)
+        coo, vals = synth.make_coo(dims, 3000, (1.1,) * N, seed=N)
+        c, v = coo.numpy(), vals.numpy()
+        p = Plan(c, v, dims, 8, host_only=True, element_bytes=16)
+        assert p.info()["elem_bytes"] == 16
+        order = O.canonical_order(c, 0)
+        want = O.flycoo_pack(c[order], v[order], dims)
+        assert np.array_equal(p.raw_elements().view(np.uint32), want), dims
+        idx, val = p.elements()
+        wi, wv = O.elements_in_order(c, v, 0)
+        assert np.array_equal(idx, wi) and np.array_equal(val.view(np.uint32), wv.view(np.uint32))
+        p.close()
+
+
+def test_packed_nonzeros_need_96_bits_at_most():
+    dims = (2 ** 31 - 1,) * 4  # 4 x 31 bits do not fit
+    coo = np.array([[0, 0, 0, 0], [1, 1, 1, 1]], np.int64)
+    with pytest.raises(SpmError) as ei:
+        Plan(coo, np.ones(2, np.float32), dims, 4, host_only=True, element_bytes=16)
+    assert ei.value.status == -1

@@ -260,3 +260,49 @@ def test_fused_and_plain_forward_give_the_same_loss_and_gradients(dtype, R):
     idx1, _ = p.elements()
     assert np.array_equal(idx0, idx1)
     p.close()
+
+
+@pytest.mark.parametrize("dims,R", [((200, 150, 100), 16), ((40, 30, 20, 10), 8)])
+def test_als_loop_graph_matches_single_iterations_and_stops_on_the_device(dims, R):
+    """cp_als_run: max_iters iterations in one graph launch give the same fits and
+    factors as that many cp_als_iter calls (the same kernels in the same order),
+    within the oracle's 1e-5; a loose tol stops after two iterations, decided on
+    the device."""
+    N = len(dims)
+    coo, vals = synth.make_coo(dims, 30_000 if N == 3 else 6_000, (0.0,) * N, seed=77 + N)
+    c, v = coo.numpy(), vals.numpy()
+    F0 = synth.make_factors(dims, R, seed=78)
+    pa = Plan(c, v, dims, R)
+    pb = Plan(c, v, dims, R)
+    Fa = [f.cuda() for f in F0]
+    Fb = [f.cuda() for f in F0]
+    la, lb = torch.empty(R, device="cuda"), torch.empty(R, device="cuda")
+    fits = pa.als_run(Fa, la, 5, 0.0)
+    ref = [pb.als_iter(Fb, lb) for _ in range(5)]
+    assert len(fits) == 5
+    assert fits == ref
+    for k in range(N):
+        assert torch.equal(Fa[k], Fb[k]), k
+    assert torch.equal(la, lb)
+    Fo = [f.numpy().astype(np.float64) for f in F0]
+    for it in range(5):
+        Fo, lo, fo = O.cp_als_iter(c, v, dims, Fo)
+        assert abs(fits[it] - fo) <= 1e-5, (it, fits[it], fo)
+    for k in range(N):
+        assert O.relerr(Fa[k].cpu().numpy(), Fo[k]) <= 1e-5, k
+    # a second call replays the graph: five more iterations continue from there
+    more = pa.als_run(Fa, la, 5, 0.0)
+    assert len(more) == 5 and all(b >= a - 1e-6 for a, b in zip(more, more[1:]))
+    # tol larger than any change: the device stops the loop after two iterations
+    G = [f.cuda() for f in F0]
+    two = pa.als_run(G, la, 10, 1.0)
+    assert len(two) == 2
+    # the working copy is still consistent after the loop
+    outs = [torch.empty(d, R, device="cuda") for d in dims]
+    pa.sweep(G, outs)
+    torch.cuda.synchronize()
+    Gh = [g.cpu().numpy().astype(np.float64) for g in G]
+    for n in range(N):
+        assert O.relerr(outs[n].cpu().numpy(), O.mttkrp(c, v, dims, Gh, n)) <= 1e-5, n
+    pa.close()
+    pb.close()

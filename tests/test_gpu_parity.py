@@ -267,3 +267,63 @@ def test_device_memory_cap_is_a_status():
     assert O.relerr(out.cpu().numpy().astype(np.float64),
                     O.mttkrp(c, v, dims, [f.cpu().numpy() for f in F], 0)) <= 1e-5
     p.close()
+
+
+@pytest.mark.parametrize("dims,dtype,R", [((60, 45, 30, 20), "f32", 32),
+                                          ((60, 45, 30, 20), "bf16", 32),
+                                          ((30, 20, 12, 8, 6), "f32", 16),
+                                          ((20, 15, 9, 7, 5, 4), "f32", 64),
+                                          ((20, 15, 9, 7, 5, 4), "bf16", 16)])
+def test_packed_16_byte_nonzeros_4_to_6_modes(dims, dtype, R):
+    """Indices packed into bit fields (16-byte nonzeros, Section 3.5): the remapped
+    working copy equals the oracle's order after every mode, outputs match the
+    oracle, the device-built plan equals the host-built one byte for byte, and
+    the device consistency check passes on the packed copy."""
+    N = len(dims)
+    coo, vals = synth.make_coo(dims, 5000, (1.1,) * N, seed=300 + N)
+    c, v = coo.numpy(), vals.numpy()
+    p, got, F, Fh = run_all_modes(coo, vals, dims, R, dtype=dtype, nblk=31, element_bytes=16)
+    assert p.info()["elem_bytes"] == 16
+    for n in range(N):
+        assert np.all(np.isfinite(got[n])), n
+        assert O.relerr(got[n], O.mttkrp(c, v, dims, Fh, n)) <= F32_TOL, n
+    p.check()
+    ph = Plan(c, v, dims, R, dtype=dtype, element_bytes=16, plan_on_host=True)
+    pd = Plan(c, v, dims, R, dtype=dtype, element_bytes=16)
+    assert np.array_equal(ph.raw_elements(), pd.raw_elements())
+    order = O.canonical_order(c, 0)
+    assert np.array_equal(pd.raw_elements().view(np.uint32), O.flycoo_pack(c[order], v[order], dims))
+    for n in range(N):
+        assert np.array_equal(pd.next_pos(n), O.next_pos(c, n).astype(np.int32))
+    ph.close()
+    pd.close()
+    p.close()
+
+
+def test_packed_nonzeros_cp_loss_and_als():
+    """CP loss (plain forward + full backward) and CP-ALS on a packed 5-mode plan
+    against the oracle."""
+    from paper_2405_08470_gb300.cp import CPLoss
+    dims, R = (30, 20, 12, 8, 6), 8
+    coo, _ = synth.make_coo(dims, 4000, (1.1,) * 5, seed=17)
+    x = synth.make_planted_targets(coo, dims, 4, 0.1, seed=18)
+    c, xv = coo.numpy(), x.numpy()
+    F = synth.make_factors(dims, R, seed=19, scale=0.3)
+    p = Plan(c, xv, dims, R, element_bytes=16, nblk=13)
+    Fd = [f.cuda().requires_grad_(True) for f in F]
+    loss = CPLoss.apply(p, *Fd)
+    loss.backward()
+    F64 = [f.numpy().astype(np.float64) for f in F]
+    want, _ = O.cp_loss(c, xv, F64)
+    assert abs(loss.item() - want) <= 1e-5 * abs(want)
+    G = O.cp_loss_grad(c, xv, dims, F64)
+    for k in range(5):
+        assert O.relerr(Fd[k].grad.cpu().numpy().astype(np.float64), G[k]) <= 1e-5, k
+    Fa = [f.clone().cuda() for f in F]
+    lam = torch.empty(R, device="cuda")
+    Fo = F64
+    for it in range(3):
+        fit = p.als_iter(Fa, lam)
+        Fo, lo, fo = O.cp_als_iter(c, xv, dims, Fo)
+        assert abs(fit - fo) <= 1e-5, (it, fit, fo)
+    p.close()

@@ -346,6 +346,26 @@ def test_hot_rows_are_the_most_frequent():
                             assert deg[r] > deg[s] or (deg[r] == deg[s] and r < s)
 
 
+def test_flycoo_pack_round_trip_and_widths():
+    """Every index comes back from its bit field (shift and mask by hand), the
+    widths are the ceil(log2 I) of the memory formula, and the value is word 3."""
+    rng = np.random.default_rng(3)
+    dims = (1000, 3, 1, 70000, 2)
+    coo = np.stack([rng.integers(0, d, 50) for d in dims], 1)
+    vals = rng.random(50).astype(np.float32)
+    w = O.flycoo_pack(coo, vals, dims)
+    assert [O.index_bits(d) for d in dims] == [10, 2, 1, 17, 1]
+    for e in range(50):
+        field = int(w[e, 0]) | (int(w[e, 1]) << 32) | (int(w[e, 2]) << 64)
+        off = 0
+        for k, d in enumerate(dims):
+            b = O.index_bits(d)
+            assert (field >> off) & ((1 << b) - 1) == coo[e, k]
+            off += b
+        assert field >> off == 0
+        assert w[e, 3] == vals[e:e + 1].view(np.uint32)[0]
+
+
 def test_flycoo_memory_formula():
     # Section 3.5.1: N log2|X| + sum log2 I_h + value bits
     assert O.flycoo_bits(2 ** 20, [2 ** 10] * 3) == pytest.approx(3 * 20 + 30 + 32)
