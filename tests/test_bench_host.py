@@ -30,7 +30,10 @@ def test_traffic_only_for_the_captured_configuration():
     for k in cfg:
         other = dict(cfg, **{k: cfg[k] + 1})
         assert bench.ncu_traffic("c2", 32, "f32", nnz, other) is None, k
-    assert bench.ncu_traffic("c2", 32, "bf16", nnz, cfg) is None
+    # each factor type reads its own entry; a rank without an entry has none
+    eb = d["entries"].get("c2_R32_bf16")
+    want_bf16 = None if eb is None else eb["dram_bytes_per_nonzero_per_launch"] * nnz
+    assert bench.ncu_traffic("c2", 32, "bf16", nnz, cfg) == want_bf16
     assert bench.ncu_traffic("c2", 64, "f32", nnz, cfg) is None
 
 
