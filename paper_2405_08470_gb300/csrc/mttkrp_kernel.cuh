@@ -166,6 +166,32 @@ struct Landing<T, 1, RC> {
 // value in the pass (so `out` receives the mode-n gradient of L = 1/2 sum e^2),
 // the remapped copy written is the residual copy (the value word holds e), and
 // every block leaves its FP64 partial of sum e^2 in loss_part.
+// Sums four per-lane partials m[0..3] over the L >= 4 lanes of a lane group
+// (lane `sub` of the group; gmask: the group's lanes) and leaves the four totals
+// in every lane.  A butterfly per value takes 4 log2(L) shuffles; here the lanes
+// first split the values over the two highest lane bits (each keeps the half the
+// partner passes), add over the remaining bits, and gather the totals back:
+// log2(L) + 4 shuffles.  Every total adds the same pairs in the same order as
+// the butterfly (xor L/2 first, then L/4, ...), so the results are bit-identical.
+__device__ __forceinline__ void group_sum4(float (&m)[4], int sub, int L, unsigned gmask) {
+  const int h = L >> 1, q = L >> 2;
+  const bool bh = (sub & h) != 0, bq = (sub & q) != 0;
+  // bit h: lanes with it clear keep values 0 and 1, the others 2 and 3
+  const float k0 = (bh ? m[2] : m[0]) + __shfl_xor_sync(gmask, bh ? m[0] : m[2], h);
+  const float k1 = (bh ? m[3] : m[1]) + __shfl_xor_sync(gmask, bh ? m[1] : m[3], h);
+  // bit q: keep one of the two (value 2 bh + bq)
+  float t = (bq ? k1 : k0) + __shfl_xor_sync(gmask, bq ? k0 : k1, q);
+  for (int off = q >> 1; off > 0; off >>= 1) t += __shfl_xor_sync(gmask, t, off);
+  // gather: the partner across bit q holds value 2 bh + !bq, across bit h 2 !bh + ..
+  const float t2 = __shfl_xor_sync(gmask, t, q);
+  const float lo = bq ? t2 : t, hi = bq ? t : t2;
+  const float lo2 = __shfl_xor_sync(gmask, lo, h), hi2 = __shfl_xor_sync(gmask, hi, h);
+  m[0] = bh ? lo2 : lo;
+  m[1] = bh ? hi2 : hi;
+  m[2] = bh ? lo : lo2;
+  m[3] = bh ? hi : hi2;
+}
+
 template <int NT, typename T, int VW, int RC, int U, int MODE, int ESB = 0, bool LOSS = false>
 __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LOSS) ? 3 : 2))
     mttkrp_warp_kernel(const MttkrpArgs a, const int L) {
@@ -410,23 +436,41 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
     if constexpr (LOSS) {
       // the residual of each nonzero: m_e = sum over the lanes of the group of
       // sum_q A_k1 A_k2 A_n, then e = m_e - x_e replaces the value
-      float sq = 0.f;
+      float m[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
+        m[u] = 0.f;
         if (u < nb) {
           float p[NV], x[NV], y[NV];
           Landing<T, VW, RC>::unpack(raw[u][0], p);
           Landing<T, VW, RC>::unpack(raw[u][1], x);
           Landing<T, VW, RC>::unpack(rown[u], y);
-          float m = 0.f;
 #pragma unroll
-          for (int q = 0; q < NV; ++q) m = fmaf(p[q] * x[q], y[q], m);
-          if (!lane_live) m = 0.f;
-          // the group's lanes run together (their segment lengths agree), other
-          // groups may be on another batch size: shuffle within the group only
-          const unsigned gmask = L >= 32 ? 0xffffffffu : (((1u << L) - 1u) << (gw * L));
-          for (int off = L / 2; off > 0; off >>= 1) m += __shfl_xor_sync(gmask, m, off);
-          const float r = m - vals[u];
+          for (int q = 0; q < NV; ++q) m[u] = fmaf(p[q] * x[q], y[q], m[u]);
+          if (!lane_live) m[u] = 0.f;
+        }
+      }
+      // the group's lanes run together (their segment lengths agree), other
+      // groups may be on another batch size: shuffle within the group only
+      const unsigned gmask = L >= 32 ? 0xffffffffu : (((1u << L) - 1u) << (gw * L));
+      if constexpr (U == 4) {
+        if (L >= 4) {
+          group_sum4(m, sub, L, gmask);
+        } else {
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            for (int off = L / 2; off > 0; off >>= 1) m[u] += __shfl_xor_sync(gmask, m[u], off);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          for (int off = L / 2; off > 0; off >>= 1) m[u] += __shfl_xor_sync(gmask, m[u], off);
+      }
+      float sq = 0.f;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (u < nb) {
+          const float r = m[u] - vals[u];
           vals[u] = r;
           sq = fmaf(r, r, sq);
           if (sub == 0)  // the residual copy: the staged nonzero's value becomes e
