@@ -17,8 +17,11 @@ int launch_als_solve(const float* M, float* U, const float* vinv, int64_t I, int
                      double* colsq, const int* status, int nb, cudaStream_t s);
 int launch_als_lambda(const double* colsq, int nb, int R, double* lam64, float* lam_out,
                       const int* status, cudaStream_t s);
-int launch_als_scale(const float* U, const float* M, void* A, int dtype, const double* lam64,
-                     int64_t I, int R, double* mdot, const int* status, int nb, cudaStream_t s);
+// R <= 64: U is not read (nor written by launch_als_solve, which then leaves the
+// column norms only); the scale pass forms M V^-1 again from M and vinv.
+int launch_als_scale(const float* U, const float* M, const float* vinv, void* A, int dtype,
+                     const double* lam64, int64_t I, int R, double* mdot, const int* status,
+                     int nb, cudaStream_t s);
 int launch_als_fit(const double* grams, int N, int R, const double* lam64, const double* mdot,
                    int nb, double normx2, double* fit_out, const int* status, cudaStream_t s);
 int launch_cp_fwd(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N,

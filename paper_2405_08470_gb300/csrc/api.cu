@@ -530,6 +530,9 @@ int spmttkrp_plan_destroy(spmttkrp_plan_t p) {
   dfree(p->d_fits);
   dfree(p->d_lpart);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->als_side) cudaStreamDestroy(p->als_side);
+  if (p->als_fork) cudaEventDestroy(p->als_fork);
+  if (p->als_join) cudaEventDestroy(p->als_join);
   p->destroyed = true;
   delete p;
   return SPM_OK;

@@ -39,18 +39,24 @@ static int ensure_als(spmttkrp_plan* p) {
   if (!p->red_nb) p->red_nb = std::max(1, p->num_sms * 8);
   int st;
   if ((st = ensure(p, (void**)&p->d_M, I * R * 4))) return st;
-  if ((st = ensure(p, (void**)&p->d_U, I * R * 4))) return st;
+  if (R > 64 && (st = ensure(p, (void**)&p->d_U, I * R * 4))) return st;  // M V^-1 (R > 64)
   if ((st = ensure(p, (void**)&p->d_gram, N * R * R * 8))) return st;
   if ((st = ensure(p, (void**)&p->d_gpart, (size_t)gram_chunks((int)R) * R * R * 8))) return st;
   if ((st = ensure(p, (void**)&p->d_red, (size_t)2 * p->red_nb * R * 8))) return st;
-  if ((st = ensure(p, (void**)&p->d_chol, 3 * R * R * 8))) return st;
+  if ((st = ensure(p, (void**)&p->d_chol, 2 * R * R * 8))) return st;
   if ((st = ensure(p, (void**)&p->d_vinv, R * R * 4))) return st;
   if ((st = ensure(p, (void**)&p->d_scal, (8 + R) * 8))) return st;
+  if (!p->als_side) SPM_CUDA(cudaStreamCreateWithFlags(&p->als_side, cudaStreamNonBlocking));
+  if (!p->als_fork) SPM_CUDA(cudaEventCreateWithFlags(&p->als_fork, cudaEventDisableTiming));
+  if (!p->als_join) SPM_CUDA(cudaEventCreateWithFlags(&p->als_join, cudaEventDisableTiming));
   return SPM_OK;
 }
 
 // Queues one CP-ALS iteration (modes 0..N-1) on p->stream.  The working copy
-// must be in mode-0 order; afterwards it is again.
+// must be in mode-0 order; afterwards it is again.  Mode n's spMTTKRP needs the
+// factors but not their Grams, so the Gram of the factor just updated and the
+// next mode's Cholesky run on a side stream beside it (forked from and joined
+// into p->stream; under stream capture they become a parallel branch).
 static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda) {
   const int N = p->N, R = p->R;
   int* status = reinterpret_cast<int*>(p->d_scal);
@@ -58,28 +64,41 @@ static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda) {
   double* lam64 = p->d_scal + 8;
   double* colsq = p->d_red;
   double* mdot = p->d_red + (size_t)p->red_nb * R;
-  cudaStream_t s = p->stream;
+  cudaStream_t s = p->stream, side = p->als_side;
   SPM_CUDA(cudaMemsetAsync(p->d_scal, 0, 8, s));
   int st;
   for (int k = 0; k < N; ++k)
     if ((st = launch_gram(factors[k], p->dtype, p->dims[(size_t)k], R, p->d_gpart, gram_chunks(R),
                           p->d_gram + (size_t)k * R * R, s)))
       return st;
+  // side: mode 0's Cholesky
+  SPM_CUDA(cudaEventRecord(p->als_fork, s));
+  SPM_CUDA(cudaStreamWaitEvent(side, p->als_fork, 0));
+  if ((st = launch_als_prep(p->d_gram, N, 0, R, p->d_chol, p->d_vinv, status, side))) return st;
+  SPM_CUDA(cudaEventRecord(p->als_join, side));
   std::vector<const void*> cf(factors, factors + N);
   for (int n = 0; n < N; ++n) {
     const int64_t I = p->dims[(size_t)n];
     if ((st = compute_mode(p, n, cf.data(), p->d_M, false))) return st;
-    if ((st = launch_als_prep(p->d_gram, N, n, R, p->d_chol, p->d_vinv, status, s))) return st;
+    SPM_CUDA(cudaStreamWaitEvent(s, p->als_join, 0));  // V^-1 of mode n is ready
     if ((st = launch_als_solve(p->d_M, p->d_U, p->d_vinv, I, R, colsq, status, p->red_nb, s)))
       return st;
     if ((st = launch_als_lambda(colsq, p->red_nb, R, lam64, lambda, status, s))) return st;
-    if ((st = launch_als_scale(p->d_U, p->d_M, factors[n], p->dtype, lam64, I, R, mdot, status,
-                               p->red_nb, s)))
+    if ((st = launch_als_scale(p->d_U, p->d_M, p->d_vinv, factors[n], p->dtype, lam64, I, R,
+                               mdot, status, p->red_nb, s)))
       return st;
+    // side: the updated factor's Gram, then the next mode's Cholesky
+    SPM_CUDA(cudaEventRecord(p->als_fork, s));
+    SPM_CUDA(cudaStreamWaitEvent(side, p->als_fork, 0));
     if ((st = launch_gram(factors[n], p->dtype, I, R, p->d_gpart, gram_chunks(R),
-                          p->d_gram + (size_t)n * R * R, s)))
+                          p->d_gram + (size_t)n * R * R, side)))
       return st;
+    if (n + 1 < N &&
+        (st = launch_als_prep(p->d_gram, N, n + 1, R, p->d_chol, p->d_vinv, status, side)))
+      return st;
+    SPM_CUDA(cudaEventRecord(p->als_join, side));
   }
+  SPM_CUDA(cudaStreamWaitEvent(s, p->als_join, 0));
   return launch_als_fit(p->d_gram, N, R, lam64, mdot, p->red_nb, p->normx2, fit, status, s);
 }
 

@@ -95,6 +95,10 @@ struct spmttkrp_plan {
   size_t max_bytes = 0, dev_bytes = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // internal stream used only for graph capture
+  // CP-ALS: a side stream that forms each updated factor's Gram and the next
+  // mode's Cholesky beside that mode's spMTTKRP, and its fork / join events
+  cudaStream_t als_side = nullptr;
+  cudaEvent_t als_fork = nullptr, als_join = nullptr;
   int device = 0;
   int num_sms = 148;
 
@@ -129,12 +133,12 @@ struct spmttkrp_plan {
   int* d_err = nullptr;      // device error word [0] and the tile form's block counter [1]
   // ALS / CP-loss scratch (allocated on first use)
   float* d_M = nullptr;       // max_n dims[n] x R: spMTTKRP output of the ALS mode
-  float* d_U = nullptr;       // max_n dims[n] x R: M V^-1 before normalisation
+  float* d_U = nullptr;       // max_n dims[n] x R: M V^-1 before normalisation (R > 64)
   double* d_gram = nullptr;   // N x R x R Gram matrices
   double* d_gpart = nullptr;  // kGramChunks x R x R Gram partials
   double* d_red = nullptr;    // 2 x red_nb x R reduction partials
   int red_nb = 0;             // blocks of the row-wise ALS kernels (fixed per plan)
-  double* d_chol = nullptr;   // 3 x R x R FP64 Cholesky work
+  double* d_chol = nullptr;   // 2 x R x R FP64 Cholesky work (R > 64)
   double* d_scal = nullptr;   // [0] status (as int), [1] fit, [2] loss, [8..8+R) lambda
   float* d_vinv = nullptr;    // R x R
   int res_valid = 0;          // residual copy d_elem[2] is current (after cp_loss_fwd)

@@ -3,6 +3,8 @@
 //   G_k = A_k^T A_k            FP32 per-chunk partials, FP64 fixed-order sum
 //   V   = Hadamard_{k!=n} G_k  FP64, Cholesky V = L L^T and V^-1 in FP64
 //   U   = M_n V^-1             FP32 (V^-1 stored as FP32), column norms^2
+//                              (R <= 64: U stays on chip; the scale pass
+//                              forms it again from M_n)
 //   lambda = sqrt(sum_i U^2)   FP64 fixed-order sum
 //   A_n = U / lambda           stored as the factor type (FP32 or BF16)
 //   fit from |X|^2, lambda, the G_k and <X, Y> (last mode).
@@ -74,47 +76,8 @@ __global__ void __launch_bounds__(256) gram_partial_kernel(const T* __restrict__
   }
 }
 
-// One warp per entry: lane l sums chunks l, l+32, ... in order, then a fixed
-// tree over the lanes (deterministic for a given chunk count).
-// R <= 32: each warp streams rows of its chunk (lane l holds A[i][l]) and adds
-// the row's outer product to 32 register accumulators (A[i][s] broadcast by
-// shuffle); the 8 warps' sums are combined in warp order.  Same chunking as the
-// tiled form, FP32 within a chunk.
-template <typename T>
-__global__ void __launch_bounds__(256) gram_warp_kernel(const T* __restrict__ A, int64_t I, int R,
-                                                        int64_t rows_per_chunk,
-                                                        double* __restrict__ part) {
-  __shared__ float red[8][32][33];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t lo = (int64_t)blockIdx.x * rows_per_chunk;
-  const int64_t hi = min(I, lo + rows_per_chunk);
-  float acc[32];
-#pragma unroll
-  for (int t = 0; t < 32; ++t) acc[t] = 0.f;
-  constexpr int RW = 4;  // rows per warp and step (loads in flight together)
-  for (int64_t i0 = lo + w; i0 < hi; i0 += 8 * RW) {
-    float a[RW];
-#pragma unroll
-    for (int q = 0; q < RW; ++q) {
-      const int64_t i = i0 + 8 * q;
-      a[q] = (i < hi && lane < R) ? to_f<T>(A[i * R + lane]) : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < RW; ++q)
-#pragma unroll
-      for (int t = 0; t < 32; ++t) acc[t] = fmaf(a[q], __shfl_sync(0xffffffffu, a[q], t), acc[t]);
-  }
-#pragma unroll
-  for (int t = 0; t < 32; ++t) red[w][lane][t] = acc[t];
-  __syncthreads();
-  for (int q = threadIdx.x; q < R * R; q += 256) {
-    const int r = q / R, c = q % R;
-    float v = 0.f;
-    for (int k = 0; k < 8; ++k) v += red[k][r][c];
-    part[(size_t)blockIdx.x * R * R + q] = (double)v;
-  }
-}
-
+// gram_reduce: one warp per entry; lane l sums chunks l, l+32, ... in order,
+// then a fixed tree over the lanes (deterministic for a given chunk count).
 __global__ void gram_reduce_kernel(const double* __restrict__ part, int nchunk, int R,
                                    double* __restrict__ G) {
   const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -127,14 +90,103 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nchunk, 
   if (lane == 0) G[q] = s;
 }
 
+// R <= 64 (RP = 16, 32 or 64 columns, zero-padded): the chunk's rows are staged
+// in shared memory 64 at a time (the next tile's loads are issued into registers
+// before the current tile is used).  G is symmetric, so only its 4 x 4 blocks on
+// and above the diagonal are formed: thread q of group g adds the outer-product
+// block (r0.., c0..), r0 <= c0, of rows g, g + NG, ... of each tile; the NG
+// groups' sums are added in group order and mirrored below the diagonal.  FP32
+// within a chunk.
+template <typename T, int RP>
+__global__ void __launch_bounds__(256) gram_tile_kernel(const T* __restrict__ A, int64_t I, int R,
+                                                        int64_t rows_per_chunk,
+                                                        double* __restrict__ part) {
+  constexpr int RT = 64, LD = RP + 4;        // tile rows; row stride keeps float4 alignment
+  constexpr int CB = RP / 4;                 // 4-column blocks per side
+  constexpr int NB = CB * (CB + 1) / 2;      // blocks on and above the diagonal
+  constexpr int NG = 256 / NB;               // thread groups (25, 7 or 1)
+  constexpr int PT = RT * RP / 256;          // tile values each thread loads
+  constexpr int TILE = RT * LD, RED = NG * RP * RP;
+  __shared__ __align__(16) float sm[TILE > RED ? TILE : RED];
+  const int tid = threadIdx.x, g = tid / NB;
+  int bi = 0, t = tid % NB;
+  while (t >= CB - bi) {
+    t -= CB - bi;
+    ++bi;
+  }
+  const int r0 = 4 * bi, c0 = 4 * (bi + t);
+  const bool active = g < NG;
+  const int64_t lo = (int64_t)blockIdx.x * rows_per_chunk;
+  const int64_t hi = min(I, lo + rows_per_chunk);
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  float pre[PT];
+  auto fetch = [&](int64_t base) {
+#pragma unroll
+    for (int p = 0; p < PT; ++p) {
+      const int e = tid + 256 * p, rr = e / RP, cc = e % RP;
+      const int64_t row = base + rr;
+      pre[p] = (row < hi && cc < R) ? to_f<T>(A[row * R + cc]) : 0.f;
+    }
+  };
+  if (lo < hi) fetch(lo);
+  for (int64_t base = lo; base < hi; base += RT) {
+    __syncthreads();  // the previous tile's reads are done
+#pragma unroll
+    for (int p = 0; p < PT; ++p) {
+      const int e = tid + 256 * p;
+      sm[(e / RP) * LD + e % RP] = pre[p];
+    }
+    __syncthreads();
+    if (base + RT < hi) fetch(base + RT);
+    if (active) {
+      for (int rr = g; rr < RT; rr += NG) {
+        const float4 x = *reinterpret_cast<const float4*>(&sm[rr * LD + r0]);
+        const float4 y = *reinterpret_cast<const float4*>(&sm[rr * LD + c0]);
+        const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xv[a], yv[b], acc[a][b]);
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) sm[(g * RP + r0 + a) * RP + c0 + b] = acc[a][b];
+  }
+  __syncthreads();
+  for (int e = tid; e < R * R; e += 256) {
+    const int r = e / R, c = e % R;
+    const int u = min(r, c), w = max(r, c);  // the entry's place on or above the diagonal
+    float v = 0.f;
+    for (int k = 0; k < NG; ++k) v += sm[(k * RP + u) * RP + w];
+    part[(size_t)blockIdx.x * R * R + e] = (double)v;
+  }
+}
+
 // ---- V = Hadamard of the other Grams, Cholesky, V^-1 (one block, FP64)
+// Every step is spread over the block, so no thread runs a long dependent chain:
+//   Cholesky, right-looking: column j is scaled by 1 / sqrt(V_jj), then the
+//     trailing lower triangle takes the rank-1 update -L_ij L_kj;
+//   X = L^-1 by forward substitution on the identity, row i at step i (scaled
+//     by 1 / L_ii), the rows below updated in parallel;
+//   V^-1 = X^T X.
+// V (holding L) and X live in dynamic shared memory when it holds them
+// (in_smem; R <= 64), else in the global work buffer.
 __global__ void __launch_bounds__(256) als_prep_kernel(const double* __restrict__ grams, int N,
                                                        int n, int R, double* __restrict__ work,
                                                        float* __restrict__ vinv,
-                                                       int* __restrict__ status) {
-  double* V = work;
-  double* L = work + (size_t)R * R;
-  double* Li = work + (size_t)2 * R * R;
+                                                       int* __restrict__ status, int in_smem) {
+  extern __shared__ double prep_smem[];
+  double* V = in_smem ? prep_smem : work;
+  double* X = V + (size_t)R * R;
   __shared__ int bad;
   __shared__ double rdiag[256];  // 1 / L[j][j] (R <= 256): FP64 divides are slow
   const int tid = threadIdx.x;
@@ -146,29 +198,29 @@ __global__ void __launch_bounds__(256) als_prep_kernel(const double* __restrict_
     for (int k = 0; k < N; ++k)
       if (k != n) v *= grams[(size_t)k * R * R + q];
     V[q] = v;
-    L[q] = 0.0;
-    Li[q] = 0.0;
+    X[q] = (q / R == q % R) ? 1.0 : 0.0;
   }
   __syncthreads();
   for (int j = 0; j < R; ++j) {
     if (tid == 0) {
-      double d = V[(size_t)j * R + j];
-      for (int k = 0; k < j; ++k) d -= L[(size_t)j * R + k] * L[(size_t)j * R + k];
+      const double d = V[(size_t)j * R + j];
       if (!(d > 0.0) || !isfinite(d)) {
         bad = 1;
       } else {
         const double l = sqrt(d);
-        L[(size_t)j * R + j] = l;
+        V[(size_t)j * R + j] = l;
         rdiag[j] = 1.0 / l;
       }
     }
     __syncthreads();
     if (bad) break;
     const double rj = rdiag[j];
-    for (int i = j + 1 + tid; i < R; i += blockDim.x) {
-      double s = V[(size_t)i * R + j];
-      for (int k = 0; k < j; ++k) s -= L[(size_t)i * R + k] * L[(size_t)j * R + k];
-      L[(size_t)i * R + j] = s * rj;
+    for (int i = j + 1 + tid; i < R; i += blockDim.x) V[(size_t)i * R + j] *= rj;
+    __syncthreads();
+    const int m = R - j - 1;  // trailing block: rows and columns j+1 .. R-1
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k <= i) V[(size_t)i * R + k] -= V[(size_t)i * R + j] * V[(size_t)k * R + j];
     }
     __syncthreads();
   }
@@ -176,21 +228,22 @@ __global__ void __launch_bounds__(256) als_prep_kernel(const double* __restrict_
     if (tid == 0) *status = SPM_ERR_NOT_SPD;
     return;
   }
-  // L^-1 column by column (lower triangular)
-  for (int c = tid; c < R; c += blockDim.x) {
-    Li[(size_t)c * R + c] = rdiag[c];
-    for (int i = c + 1; i < R; ++i) {
-      double s = 0.0;
-      for (int k = c; k < i; ++k) s += L[(size_t)i * R + k] * Li[(size_t)k * R + c];
-      Li[(size_t)i * R + c] = -s * rdiag[i];
+  for (int i = 0; i < R; ++i) {
+    const double ri = rdiag[i];
+    for (int c = tid; c <= i; c += blockDim.x) X[(size_t)i * R + c] *= ri;
+    __syncthreads();
+    const int rows = R - i - 1, cols = i + 1;
+    for (int e = tid; e < rows * cols; e += blockDim.x) {
+      const int k = i + 1 + e / cols, c = e % cols;
+      X[(size_t)k * R + c] -= V[(size_t)k * R + i] * X[(size_t)i * R + c];
     }
+    __syncthreads();
   }
-  __syncthreads();
-  // V^-1 = L^-T L^-1
+  // V^-1 = X^T X (X lower triangular)
   for (int q = tid; q < R * R; q += blockDim.x) {
     const int i = q / R, j = q % R;
     double s = 0.0;
-    for (int k = max(i, j); k < R; ++k) s += Li[(size_t)k * R + i] * Li[(size_t)k * R + j];
+    for (int k = max(i, j); k < R; ++k) s += X[(size_t)k * R + i] * X[(size_t)k * R + j];
     vinv[q] = (float)s;
   }
 }
@@ -271,6 +324,92 @@ __global__ void __launch_bounds__(256) als_solve_kernel(const float* __restrict_
     double s = 0.0;
     for (int q = 0; q < 8; ++q) s += (double)wsum[q][r];
     colsq_part[(size_t)blockIdx.x * R + r] = s;
+  }
+}
+
+// R <= 64 (RP = 16, 32 or 64 columns, zero-padded): U = M V^-1 on row tiles
+// staged in shared memory.  Thread (rs, cb) holds the 4 x 4 block of rows rs +
+// RS k and columns 4 cb..; every entry adds m_ij V^-1_jr over j in ascending
+// order with fmaf, as the warp-per-row kernel does.
+//   SCALE = false: per-block column sums of U^2 (for lambda); U is not stored.
+//   SCALE = true:  U is formed again from M (the same arithmetic, so the same
+//                  values), A = U / lambda is stored as T, and per-block column
+//                  sums of M * A (for <X, Y>) are left in part.
+template <typename T, int RP, bool SCALE>
+__global__ void __launch_bounds__(256) als_rows_kernel(const float* __restrict__ M,
+                                                       const float* __restrict__ vinv,
+                                                       T* __restrict__ A,
+                                                       const double* __restrict__ lam64,
+                                                       int64_t I, int R,
+                                                       double* __restrict__ part,
+                                                       const int* __restrict__ status) {
+  constexpr int CB = RP / 4, RS = 256 / CB, RT = 4 * RS, LD = RP + 1;
+  __shared__ float Ms[RT * LD];
+  __shared__ __align__(16) float Vs[RP * RP];
+  __shared__ float red[RS][RP];
+  if (*status) return;
+  const int tid = threadIdx.x, cb = tid % CB, rs = tid / CB, c0 = 4 * cb;
+  for (int e = tid; e < RP * RP; e += 256) {
+    const int j = e / RP, c = e % RP;
+    Vs[e] = (j < R && c < R) ? vinv[j * R + c] : 0.f;
+  }
+  float inv[4], sum[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    inv[b] = (SCALE && c0 + b < R) ? (float)(1.0 / lam64[c0 + b]) : 0.f;
+    sum[b] = 0.f;
+  }
+  const int64_t ntiles = (I + RT - 1) / RT;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i0 = t * RT;
+    __syncthreads();  // the previous tile's reads of Ms are done
+    for (int e = tid; e < RT * RP; e += 256) {
+      const int rr = e / RP, cc = e % RP;
+      const int64_t i = i0 + rr;
+      Ms[rr * LD + cc] = (i < I && cc < R) ? M[i * R + cc] : 0.f;
+    }
+    __syncthreads();
+    float u[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) u[k][b] = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < RP; ++j) {
+      const float4 v = *reinterpret_cast<const float4*>(&Vs[j * RP + c0]);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float m = Ms[(rs + RS * k) * LD + j];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) u[k][b] = fmaf(m, vv[b], u[k][b]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = i0 + rs + RS * k;
+      if (i >= I) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = c0 + b;
+        if (c >= R) continue;
+        if constexpr (SCALE) {
+          const T a = from_f<T>(u[k][b] * inv[b]);
+          A[i * R + c] = a;
+          sum[b] = fmaf(Ms[(rs + RS * k) * LD + c], to_f<T>(a), sum[b]);
+        } else {
+          sum[b] = fmaf(u[k][b], u[k][b], sum[b]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) red[rs][c0 + b] = sum[b];
+  __syncthreads();
+  for (int c = tid; c < R; c += 256) {
+    double acc = 0.0;
+    for (int q = 0; q < RS; ++q) acc += (double)red[q][c];
+    part[(size_t)blockIdx.x * R + c] = acc;
   }
 }
 
@@ -402,13 +541,20 @@ int launch_gram(const void* A, int dtype, int64_t I, int R, double* part, int ma
   int nchunk = (int)std::max<int64_t>(1, (I + rpc - 1) / rpc);
   const int nt = (R + 31) / 32;
   dim3 grid(nchunk, nt, nt);
-  if (R <= 32) {
-    if (dtype == SPM_DTYPE_BF16)
-      gram_warp_kernel<__nv_bfloat16><<<nchunk, 256, 0, s>>>(
-          static_cast<const __nv_bfloat16*>(A), I, R, rpc, part);
-    else
-      gram_warp_kernel<float><<<nchunk, 256, 0, s>>>(static_cast<const float*>(A), I, R, rpc,
-                                                     part);
+  if (R <= 64) {
+    const bool bf = dtype == SPM_DTYPE_BF16;
+    const auto* Ab = static_cast<const __nv_bfloat16*>(A);
+    const auto* Af = static_cast<const float*>(A);
+    if (R <= 16) {
+      if (bf) gram_tile_kernel<__nv_bfloat16, 16><<<nchunk, 256, 0, s>>>(Ab, I, R, rpc, part);
+      else gram_tile_kernel<float, 16><<<nchunk, 256, 0, s>>>(Af, I, R, rpc, part);
+    } else if (R <= 32) {
+      if (bf) gram_tile_kernel<__nv_bfloat16, 32><<<nchunk, 256, 0, s>>>(Ab, I, R, rpc, part);
+      else gram_tile_kernel<float, 32><<<nchunk, 256, 0, s>>>(Af, I, R, rpc, part);
+    } else {
+      if (bf) gram_tile_kernel<__nv_bfloat16, 64><<<nchunk, 256, 0, s>>>(Ab, I, R, rpc, part);
+      else gram_tile_kernel<float, 64><<<nchunk, 256, 0, s>>>(Af, I, R, rpc, part);
+    }
   } else if (dtype == SPM_DTYPE_BF16) {
     gram_partial_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(
         static_cast<const __nv_bfloat16*>(A), I, R, rpc, part);
@@ -423,7 +569,14 @@ int launch_gram(const void* A, int dtype, int64_t I, int R, double* part, int ma
 
 int launch_als_prep(const double* grams, int N, int n, int R, double* work, float* vinv,
                     int* status, cudaStream_t s) {
-  als_prep_kernel<<<1, 256, 0, s>>>(grams, N, n, R, work, vinv, status);
+  const size_t smem = (size_t)2 * R * R * sizeof(double);
+  const int in_smem = R <= 64;
+  if (in_smem) {
+    int st = ensure_dyn_smem((const void*)als_prep_kernel, 2 * 64 * 64 * sizeof(double),
+                             "cudaFuncSetAttribute(als_prep)");
+    if (st) return st;
+  }
+  als_prep_kernel<<<1, 256, in_smem ? smem : 0, s>>>(grams, N, n, R, work, vinv, status, in_smem);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SPM_OK : cuda_fail(e, "als_prep_kernel");
 }
@@ -442,7 +595,16 @@ static int solve_cc(const float* M, float* U, const float* vinv, int64_t I, int 
 int launch_als_solve(const float* M, float* U, const float* vinv, int64_t I, int R,
                      double* colsq, const int* status, int nb, cudaStream_t s) {
   const int cc = (R + 31) / 32;
-  if (cc <= 1) solve_cc<1>(M, U, vinv, I, R, colsq, status, nb, s);
+  if (R <= 16)  // column norms only: the scale pass forms U again
+    als_rows_kernel<float, 16, false><<<nb, 256, 0, s>>>(M, vinv, nullptr, nullptr, I, R, colsq,
+                                                          status);
+  else if (R <= 32)
+    als_rows_kernel<float, 32, false><<<nb, 256, 0, s>>>(M, vinv, nullptr, nullptr, I, R, colsq,
+                                                          status);
+  else if (R <= 64)
+    als_rows_kernel<float, 64, false><<<nb, 256, 0, s>>>(M, vinv, nullptr, nullptr, I, R, colsq,
+                                                          status);
+  else if (cc <= 1) solve_cc<1>(M, U, vinv, I, R, colsq, status, nb, s);
   else if (cc <= 2) solve_cc<2>(M, U, vinv, I, R, colsq, status, nb, s);
   else if (cc <= 4) solve_cc<4>(M, U, vinv, I, R, colsq, status, nb, s);
   else solve_cc<8>(M, U, vinv, I, R, colsq, status, nb, s);
@@ -464,10 +626,28 @@ static void scale_cc(const float* U, const float* M, void* A, const double* lam6
                                              status);
 }
 
-int launch_als_scale(const float* U, const float* M, void* A, int dtype, const double* lam64,
-                     int64_t I, int R, double* mdot, const int* status, int nb, cudaStream_t s) {
+template <typename T>
+static void rows_scale(const float* M, const float* vinv, void* A, const double* lam64, int64_t I,
+                       int R, double* mdot, const int* status, int nb, cudaStream_t s) {
+  T* At = static_cast<T*>(A);
+  if (R <= 16)
+    als_rows_kernel<T, 16, true><<<nb, 256, 0, s>>>(M, vinv, At, lam64, I, R, mdot, status);
+  else if (R <= 32)
+    als_rows_kernel<T, 32, true><<<nb, 256, 0, s>>>(M, vinv, At, lam64, I, R, mdot, status);
+  else
+    als_rows_kernel<T, 64, true><<<nb, 256, 0, s>>>(M, vinv, At, lam64, I, R, mdot, status);
+}
+
+int launch_als_scale(const float* U, const float* M, const float* vinv, void* A, int dtype,
+                     const double* lam64, int64_t I, int R, double* mdot, const int* status,
+                     int nb, cudaStream_t s) {
   const int cc = (R + 31) / 32;
-  if (dtype == SPM_DTYPE_BF16) {
+  if (R <= 64) {
+    if (dtype == SPM_DTYPE_BF16)
+      rows_scale<__nv_bfloat16>(M, vinv, A, lam64, I, R, mdot, status, nb, s);
+    else
+      rows_scale<float>(M, vinv, A, lam64, I, R, mdot, status, nb, s);
+  } else if (dtype == SPM_DTYPE_BF16) {
     if (cc <= 1) scale_cc<__nv_bfloat16, 1>(U, M, A, lam64, I, R, mdot, status, nb, s);
     else if (cc <= 2) scale_cc<__nv_bfloat16, 2>(U, M, A, lam64, I, R, mdot, status, nb, s);
     else if (cc <= 4) scale_cc<__nv_bfloat16, 4>(U, M, A, lam64, I, R, mdot, status, nb, s);
