@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--nblk", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--variant", type=int, default=0,
-                    help="0 warp blocks with staged tiles, 1 CTA blocks with direct runs")
+                    help="0 warp blocks with staged tiles, 1 CTA blocks with direct runs, "
+                         "2 tile form, 3 warp blocks with a remap warp per CTA")
     ap.add_argument("--unroll", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--element-bytes", type=int, default=0)
@@ -843,7 +844,9 @@ def main():
                        "kernel_form": ["warp blocks, bulk-async staged tiles",
                                        "CTA blocks, direct runs",
                                        "persistent CTAs, 960-nonzero tiles, remap stores in "
-                                       "destination order"][info["variant"]],
+                                       "destination order",
+                                       "warp blocks, bulk-async staged tiles, one remap warp "
+                                       "per CTA storing in destination order"][info["variant"]],
                        "autotuned": bool(args.autotune),
                        "unroll": args.unroll or 8, "cache_hints": args.hints,
                        "stages": info["stages"],
@@ -861,7 +864,7 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                          "kernel": ["mttkrp_warp_kernel", "mttkrp_direct_kernel",
-                                    "mttkrp_tile_kernel"][info["variant"]] +
+                                    "mttkrp_tile_kernel", "mttkrp_warp_kernel"][info["variant"]] +
                                    " (+ split-row fix-up; CUDA events around each mode)",
                          "algorithmic_bytes_per_sweep": int(sum(byts)),
                          "no_reuse_bytes_per_sweep": int(no_reuse),

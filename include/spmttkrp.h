@@ -81,7 +81,12 @@ typedef struct {
                        16-byte aligned factors and outputs; otherwise form 0 runs):
                        persistent CTAs stage tiles of 960 consecutive nonzeros,
                        issue the remap stores in destination order, and keep
-                       several gathers in flight per lane group                 */
+                       several gathers in flight per lane group;
+                       3 = form 0 with one remap warp per CTA (3 modes, 32-byte
+                       nonzeros carrying their ids and write orders, partition
+                       0; otherwise form 0 runs): 7 warps per CTA compute and
+                       the 8th stores the CTA's 960-nonzero write-order tiles
+                       in destination order                                     */
   int unroll;       /* nonzeros in flight per lane group in form 0: 0 (= 8), 4, 8 */
   int stages;       /* tiles per warp ring in form 0: 0 (= 2 for 32-byte and wider
                        nonzeros, 3 for 16-byte ones), 2, 3 or 4                   */

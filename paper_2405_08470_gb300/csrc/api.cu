@@ -245,7 +245,7 @@ int run_mode(spmttkrp_plan* p, int mode, const void* const* factors, float* out,
   a.hot_flags = p->hot_rows > 0 && (p->hints & 4);  // read by the tile form only
   a.loss_part = loss_part;  // the fused CP-loss pass (always the warp-block form)
   if (loss_part) a.variant = 0;
-  if (a.variant == 2 && !p->worders) a.variant = 0;  // no write orders: form 0
+  if ((a.variant == 2 || a.variant == 3) && !p->worders) a.variant = 0;  // no write orders
   // the pass's elements carry their remap ids: word 4 + (next mode)
   a.alpha_word = p->alpha ? 4 + (mode + 1) % p->N : 0;
   int st = launch_mttkrp(a, p->stream);
@@ -339,8 +339,8 @@ int spmttkrp_plan_create(spmttkrp_plan_t* out, const int64_t* coo, const float* 
   if (o.tile != 0 && o.tile != 32 && o.tile != 64 && o.tile != 128 && o.tile != 256)
     return fail(SPM_ERR_INVALID_ARG, "tile must be 0, 32, 64, 128 or 256");
   if (o.nblk < 0) return fail(SPM_ERR_INVALID_ARG, "nblk must be >= 0");
-  if (o.variant < 0 || o.variant > 2)
-    return fail(SPM_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  if (o.variant < 0 || o.variant > 3)
+    return fail(SPM_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   if (o.unroll != 0 && o.unroll != 4 && o.unroll != 8)
     return fail(SPM_ERR_INVALID_ARG, "unroll must be 0, 4 or 8");
   if (o.stages != 0 && (o.stages < 2 || o.stages > 4))

@@ -42,6 +42,21 @@ int launch_mttkrp_bf16(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
       default: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 2, 32, true>(a, c.L, s);
     }
   }
+  if (a.variant == 3) {  // form 3: one remap warp per CTA (the dispatcher checked the layout)
+    if (c.VW == 4) {
+      switch (a.mode) {
+        case 0: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 8, 0, 32, false, true>(a, c.L, s);
+        case 1: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 8, 1, 32, false, true>(a, c.L, s);
+        default:
+          return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 8, 2, 32, false, true>(a, c.L, s);
+      }
+    }
+    switch (a.mode) {
+      case 0: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8, 0, 32, false, true>(a, c.L, s);
+      case 1: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8, 1, 32, false, true>(a, c.L, s);
+      default: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 8, 2, 32, false, true>(a, c.L, s);
+    }
+  }
   if (a.variant == 1) return launch_direct_bfloat16(a, c, s);
   if (c.vec && c.VW == 4) {  // 8-byte lane slices (R <= 32): the FP32 kernel's lane shape
     switch (a.nmodes) {

@@ -34,6 +34,13 @@ int launch_mttkrp_f32(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
       default: return launch_warp_kernel<3, float, 4, 1, 4, 2, 32, true>(a, c.L, s);
     }
   }
+  if (a.variant == 3) {  // form 3: one remap warp per CTA (the dispatcher checked the layout)
+    switch (a.mode) {
+      case 0: return launch_warp_kernel<3, float, 4, 1, 8, 0, 32, false, true>(a, c.L, s);
+      case 1: return launch_warp_kernel<3, float, 4, 1, 8, 1, 32, false, true>(a, c.L, s);
+      default: return launch_warp_kernel<3, float, 4, 1, 8, 2, 32, false, true>(a, c.L, s);
+    }
+  }
   if (a.variant == 1) return launch_direct_float(a, c, s);
   if (c.vec) {
     switch (a.nmodes) {

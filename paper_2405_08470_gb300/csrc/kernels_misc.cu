@@ -15,7 +15,7 @@ static LaneCfg cfg_for(const MttkrpArgs& a) {
   bool al = aligned16(a.out);
   for (int k = 0; k < a.nmodes; ++k)
     if (k != a.mode) al = al && aligned16(a.factors[k]);
-  return lane_config(a.R, a.dtype, al, a.variant == 0);
+  return lane_config(a.R, a.dtype, al, a.variant == 0 || a.variant == 3);  // form 0's lanes
 }
 
 size_t mttkrp_smem_bytes(int es, int tile, int R, int dtype, int stages) {
@@ -40,6 +40,14 @@ int launch_mttkrp(const MttkrpArgs& a, cudaStream_t s) {
       if (k != a.mode) al = al && aligned16(a.factors[k]);
     if (al && tile_form_supported(a.nmodes, a.es, a.alpha_word, a.R) && a.no_fill == 0)
       return launch_mttkrp_tile(a, s);
+    MttkrpArgs b = a;
+    b.variant = 0;
+    return a.dtype == SPM_DTYPE_BF16 ? launch_mttkrp_bf16(b, c, s) : launch_mttkrp_f32(b, c, s);
+  }
+  if (a.variant == 3 &&
+      !(c.vec && a.nmodes == 3 && a.es == 32 && a.alpha_word && a.no_fill == 0 && a.elems_out)) {
+    // form 3 needs 32-byte 3-mode nonzeros with their ids and write orders, the
+    // contiguous split, and a remap to do; otherwise form 0
     MttkrpArgs b = a;
     b.variant = 0;
     return a.dtype == SPM_DTYPE_BF16 ? launch_mttkrp_bf16(b, c, s) : launch_mttkrp_f32(b, c, s);

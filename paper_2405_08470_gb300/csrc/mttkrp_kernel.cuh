@@ -28,6 +28,7 @@
 #pragma once
 
 #include "mttkrp_common.cuh"
+#include "mttkrp_tile.cuh"  // the write-order tiles (kTileNnz, kTileWordW)
 
 namespace spm {
 
@@ -192,11 +193,111 @@ __device__ __forceinline__ void group_sum4(float (&m)[4], int sub, int L, unsign
   m[3] = bh ? hi : hi2;
 }
 
-template <int NT, typename T, int VW, int RC, int U, int MODE, int ESB = 0, bool LOSS = false>
+// RWARP (3 modes, 32-byte nonzeros carrying remap ids and write orders; form 3):
+// the CTA's last warp does the remap of the CTA's blocks, the other warps only
+// compute.  The remap warp takes the 960-nonzero write-order tiles that start in
+// the CTA's range of the mode order; it stages each with one bulk copy into its
+// shared-memory region (`region`: an mbarrier, then the tile at +128) and stores
+// the tile's nonzeros in the order of their destinations, so stores that land
+// side by side leave together.  The two roles share nothing but the input.
+constexpr int kRemapRegion = 128 + kTileNnz * 32;  // bytes of the remap warp's region
+__device__ __forceinline__ void remap_warp_tiles(const MttkrpArgs& a, int mode, int cw,
+                                                 uint8_t* region, unsigned long long wait_ns) {
+  const int lane = threadIdx.x & 31;
+  const int b0 = blockIdx.x * cw, b1 = min(b0 + cw, a.nblk) - 1;
+  if (b0 > b1) return;
+  // a tile belongs to the block holding its first nonzero; the tiles are taken
+  // in the compute warps' wavefront order: the k-th tile of each block in turn
+  int64_t ft[kWarps], et[kWarps];
+  int64_t kmax = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    ft[w] = et[w] = 0;
+    if (w < cw && b0 + w <= b1) {
+      const int4 bw = a.blkinfo[b0 + w];
+      ft[w] = ((int64_t)bw.x + kTileNnz - 1) / kTileNnz;
+      et[w] = ((int64_t)bw.y + kTileNnz - 1) / kTileNnz;
+      kmax = max(kmax, et[w] - ft[w]);
+    }
+  }
+  int64_t kk = 0;
+  int ww = -1;
+  auto next_tile = [&]() -> int64_t {  // advances (kk, ww); -1 when done
+    for (;;) {
+      if (++ww == cw) {
+        ww = 0;
+        ++kk;
+      }
+      if (kk >= kmax) return -1;
+      int64_t t = -1;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w)
+        if (w == ww && ft[w] + kk < et[w]) t = ft[w] + kk;
+      if (t >= 0) return t;
+    }
+  };
+  int64_t t = next_tile();
+  if (t < 0) return;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(region);
+  uint8_t* buf = region + 128;
+  const int nx = (mode + 1) % 3;
+  const uint64_t pol = make_policy(1);
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  auto issue = [&](int64_t t) {  // lane 0: stage tile t
+    const int64_t base = t * kTileNnz;
+    const uint32_t bytes = (uint32_t)min((int64_t)kTileNnz, a.nnz - base) * 32u;
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, bytes);
+    bulk_g2s_hint(buf, a.elems_in + base * 32, bytes, bar, make_policy(0));
+  };
+  if (lane == 0) issue(t);
+  for (uint32_t it = 0; t >= 0; ++it) {
+    const uint32_t parity = it & 1u;
+    const bool ok = mbar_wait_bounded(bar, parity, wait_ns);
+    if (!__all_sync(0xffffffffu, ok)) {
+      // the copy did not complete in time: record it, wait (bounded) for it, leave
+      if (lane == 0) {
+        if (a.err) atomicOr(a.err, 1);
+        (void)mbar_wait_bounded(bar, parity);
+      }
+      return;
+    }
+    const int len = (int)min((int64_t)kTileNnz, a.nnz - t * kTileNnz);
+    for (int j = lane; j < len; j += 32) {
+      const uint32_t wo = reinterpret_cast<const uint32_t*>(buf + (size_t)j * 32)[kTileWordW];
+      const int k = (int)((wo >> (10 * mode)) & 1023u);
+      if (k >= len) {  // damaged write order: skip and report
+        if (a.err) atomicOr(a.err, 2);
+        continue;
+      }
+      const uint4* sp = reinterpret_cast<const uint4*>(buf + (size_t)k * 32);
+      const uint4 lo4 = sp[0], hi4 = sp[1];
+      const uint32_t dst = (nx == 0 ? hi4.x : (nx == 1 ? hi4.y : hi4.z)) & kAlphaMask;
+      if ((int64_t)dst >= a.nnz) {
+        if (a.err) atomicOr(a.err, 2);
+        continue;
+      }
+      st_hint_v8(a.elems_out + (int64_t)dst * 32, lo4, hi4, pol);
+    }
+    __syncwarp();  // every lane has read the tile before the next copy lands on it
+    t = next_tile();
+    if (lane == 0 && t >= 0) issue(t);
+  }
+}
+
+template <int NT, typename T, int VW, int RC, int U, int MODE, int ESB = 0, bool LOSS = false,
+          bool RWARP = false>
 __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LOSS) ? 3 : 2))
     mttkrp_warp_kernel(const MttkrpArgs a, const int L) {
   static_assert(!LOSS || (NT == 3 && MODE >= 0 && VW > 1 && ESB == 32),
                 "the fused CP-loss pass is built for 3 modes and 32-byte nonzeros");
+  static_assert(!RWARP || (NT == 3 && MODE >= 0 && VW > 1 && ESB == 32 && !LOSS),
+                "the remap warp is built for 3 modes and 32-byte nonzeros");
+  constexpr int CW = RWARP ? kWarps - 1 : kWarps;  // warps that compute
   constexpr int NV = VW * RC;
   const int N = NT > 0 ? NT : a.nmodes;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -207,7 +308,17 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
   const int es = (NT > 0 && !a.pk.packed) ? ES_C : a.es;
   const int R = a.R, mode = MODE >= 0 ? MODE : a.mode;
   const int TW = a.tile, K = TW / G, NPK = np_stage_ints(K);
-  const int wb = blockIdx.x * kWarps + warp;
+  if constexpr (RWARP) {
+    if (warp == kWarps - 1) {
+      extern __shared__ __align__(128) uint8_t smem_r[];
+      const WarpLayout lr = warp_layout(es, TW, R, G, a.stages);
+      if (a.elems_out)
+        remap_warp_tiles(a, MODE, CW, smem_r + (size_t)CW * lr.total,
+                         a.wait_ns ? a.wait_ns : kWaitLimitNs);
+      return;
+    }
+  }
+  const int wb = blockIdx.x * CW + warp;
   if (wb >= a.nblk) return;
   const int4 bi = a.blkinfo[wb];
   const int lo = bi.x, hi = bi.y;
@@ -233,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
   const int ga = lo + (int)(len * gw / G), gb = lo + (int)(len * (gw + 1) / G);
   const int maxrun = (int)((len + G - 1) / G);
   const int ntiles = (maxrun + K - 1) / K;
-  const bool remap = a.elems_out != nullptr;
+  const bool remap = a.elems_out != nullptr && !RWARP;  // RWARP: the remap warp's work
   const bool leader = (sub == 0);
   const float sc = a.scale ? __ldg(a.scale) : 1.0f;
   const int64_t out_rows = a.out_rows;
@@ -740,16 +851,21 @@ __host__ __device__ inline int warp_tile_for(int tile, int G) {
   return G * K;
 }
 
-template <int NT, typename T, int VW, int RC, int U, int MODE = -1, int ESB = 0, bool LOSS = false>
+template <int NT, typename T, int VW, int RC, int U, int MODE = -1, int ESB = 0, bool LOSS = false,
+          bool RWARP = false>
 int launch_warp_kernel(const MttkrpArgs& a0, int L, cudaStream_t s) {
   const int G = 32 / L;
   MttkrpArgs a = a0;
   a.tile = warp_tile_for(a0.tile, G);
-  const size_t smem = (size_t)kWarps * warp_layout(a.es, a.tile, a.R, G, a.stages).total;
-  auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U, MODE, ESB, LOSS>;
+  // form 3: seven compute warps' slots, then the remap warp's region
+  const size_t smem = RWARP ? (size_t)(kWarps - 1) * warp_layout(a.es, a.tile, a.R, G, a.stages).total +
+                                  kRemapRegion
+                            : (size_t)kWarps * warp_layout(a.es, a.tile, a.R, G, a.stages).total;
+  auto kfn = mttkrp_warp_kernel<NT, T, VW, RC, U, MODE, ESB, LOSS, RWARP>;
   int st = ensure_dyn_smem((const void*)kfn, smem, "cudaFuncSetAttribute(mttkrp_warp)");
   if (st) return st;
-  const int grid = (a.nblk + kWarps - 1) / kWarps;
+  constexpr int CW = RWARP ? kWarps - 1 : kWarps;  // blocks per CTA
+  const int grid = (a.nblk + CW - 1) / CW;
   kfn<<<grid, kThreads, smem, s>>>(a, L);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "mttkrp_warp_kernel launch");

@@ -100,8 +100,8 @@ static void stable_sort_by(const int32_t* key, int64_t dim, std::vector<int32_t>
 int default_nblk(int64_t nnz, int num_sms, int variant) {
   if (nnz <= 0) return 1;
   int64_t nb;
-  if (variant == 0) {
-    // warp blocks: about 16 waves of 24 warps per SM, each block >= 256
+  if (variant == 0 || variant == 3) {
+    // warp blocks (forms 0 and 3): about 16 waves of 24 warps per SM, each block >= 256
     // nonzeros, and never more than 4K nonzeros per block (measured: blocks of
     // 1.7-4K nonzeros sweep fastest on 60M-200M nonzero tensors)
     nb = std::max<int64_t>(std::min<int64_t>((int64_t)num_sms * 24 * 16, (nnz + 255) / 256),

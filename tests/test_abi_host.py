@@ -81,7 +81,7 @@ def test_host_plan_empty_tensor():
 
 @pytest.mark.parametrize("case,status", [
     ("dup", -3), ("range", -2), ("neg", -2), ("nmodes", -1), ("rank0", -1), ("rank_big", -6),
-    ("tile", -1), ("dims0", -1), ("partition", -1), ("dtype", -1),
+    ("tile", -1), ("dims0", -1), ("partition", -1), ("dtype", -1), ("variant", -1),
 ])
 def test_host_error_paths(case, status):
     coo = np.array([[0, 1, 2], [1, 1, 1], [2, 0, 0]], np.int64)
@@ -103,6 +103,8 @@ def test_host_error_paths(case, status):
         kw["tile"] = 300
     elif case == "dims0":
         dims = (3, 0, 3)
+    elif case == "variant":
+        kw["variant"] = 4  # forms 0..3
     if case in ("partition", "dtype"):
         L = lib()
         o = binding.Opts()
