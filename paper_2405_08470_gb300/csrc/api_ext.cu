@@ -57,7 +57,10 @@ static int ensure_als(spmttkrp_plan* p) {
 // factors but not their Grams, so the Gram of the factor just updated and the
 // next mode's Cholesky run on a side stream beside it (forked from and joined
 // into p->stream; under stream capture they become a parallel branch).
-static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda) {
+// grams_current: the plan's Grams already belong to these factors (the previous
+// iteration of the same loop formed them), so none is formed first.
+static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda,
+                       bool grams_current = false) {
   const int N = p->N, R = p->R;
   int* status = reinterpret_cast<int*>(p->d_scal);
   double* fit = p->d_scal + 1;
@@ -67,7 +70,7 @@ static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda) {
   cudaStream_t s = p->stream, side = p->als_side;
   SPM_CUDA(cudaMemsetAsync(p->d_scal, 0, 8, s));
   int st;
-  for (int k = 0; k < N; ++k)
+  for (int k = 0; k < N && !grams_current; ++k)
     if ((st = launch_gram(factors[k], p->dtype, p->dims[(size_t)k], R, p->d_gpart, gram_chunks(R),
                           p->d_gram + (size_t)k * R * R, s)))
       return st;
@@ -332,7 +335,7 @@ int cp_als_run(spmttkrp_plan_t p, void* const* factors, float* lambda, int max_i
       e = cudaStreamBeginCaptureToGraph(p->stream, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        st = als_enqueue(p, factors, lambda);
+        st = als_enqueue(p, factors, lambda, t > 0);  // iteration t-1 formed the Grams
         if (!st)
           st = launch_als_converge(p->d_scal + 1, status, p->d_fits, d_iters, t, tol,
                                    t + 1 < max_iters ? h[(size_t)t + 1] : h[(size_t)t],

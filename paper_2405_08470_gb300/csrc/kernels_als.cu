@@ -419,7 +419,8 @@ __device__ __forceinline__ double warp_column_sum(const double* __restrict__ par
                                                   int r) {
   const int lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int b = lane; b < nb; b += 32) s += part[(size_t)b * R + r];
+#pragma unroll 8
+  for (int b = lane; b < nb; b += 32) s += part[(size_t)b * R + r];  // loads run ahead
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   return __shfl_sync(0xffffffffu, s, 0);
@@ -499,36 +500,42 @@ __global__ void __launch_bounds__(256) als_scale_kernel(const float* __restrict_
 }
 
 // ---- fit = 1 - sqrt(|X|^2 + |Y|^2 - 2 <X,Y>) / |X|
-__global__ void __launch_bounds__(256) als_fit_kernel(const double* __restrict__ grams, int N,
-                                                      int R, const double* __restrict__ lam64,
-                                                      const double* __restrict__ mdot_part,
-                                                      int nb, double normx2,
-                                                      double* __restrict__ fit_out,
-                                                      const int* __restrict__ status) {
-  __shared__ double red[256];
-  __shared__ double red2[256];
+// One block of kFitThreads: a warp per column of <M, A> (the column sums of the
+// per-block partials), then a fixed-order tree over the threads' parts.
+constexpr int kFitThreads = 1024;
+__global__ void __launch_bounds__(kFitThreads) als_fit_kernel(const double* __restrict__ grams,
+                                                              int N, int R,
+                                                              const double* __restrict__ lam64,
+                                                              const double* __restrict__ mdot_part,
+                                                              int nb, double normx2,
+                                                              double* __restrict__ fit_out,
+                                                              const int* __restrict__ status) {
+  __shared__ double red[kFitThreads];
+  __shared__ double red2[kFitThreads];
   const int tid = threadIdx.x;
   double y2 = 0.0, xy = 0.0;
-  for (int q = tid; q < R * R; q += 256) {
+  for (int q = tid; q < R * R; q += kFitThreads) {
     const int r = q / R, s = q % R;
     double h = 1.0;
     for (int k = 0; k < N; ++k) h *= grams[(size_t)k * R * R + q];
     y2 += lam64[r] * lam64[s] * h;
   }
-  for (int r = tid >> 5; r < R; r += 8) {  // one warp per column
+  for (int r = tid >> 5; r < R; r += kFitThreads / 32) {  // one warp per column
     const double m = warp_column_sum(mdot_part, nb, R, r);
     if ((tid & 31) == 0) xy += lam64[r] * m;
   }
   red[tid] = y2;
   red2[tid] = xy;
   __syncthreads();
-  if (tid == 0) {
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < 256; ++q) {
-      a += red[q];
-      b += red2[q];
+  for (int w = kFitThreads / 2; w > 0; w >>= 1) {
+    if (tid < w) {
+      red[tid] += red[tid + w];
+      red2[tid] += red2[tid + w];
     }
-    const double res2 = fmax(normx2 + a - 2.0 * b, 0.0);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double res2 = fmax(normx2 + red[0] - 2.0 * red2[0], 0.0);
     fit_out[0] = *status ? nan("") : 1.0 - sqrt(res2) / sqrt(normx2);
   }
 }
@@ -664,7 +671,8 @@ int launch_als_scale(const float* U, const float* M, const float* vinv, void* A,
 
 int launch_als_fit(const double* grams, int N, int R, const double* lam64, const double* mdot,
                    int nb, double normx2, double* fit_out, const int* status, cudaStream_t s) {
-  als_fit_kernel<<<1, 256, 0, s>>>(grams, N, R, lam64, mdot, nb, normx2, fit_out, status);
+  als_fit_kernel<<<1, kFitThreads, 0, s>>>(grams, N, R, lam64, mdot, nb, normx2, fit_out,
+                                           status);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SPM_OK : cuda_fail(e, "als_fit_kernel");
 }
