@@ -34,7 +34,7 @@ def _tensor():
     return dims, R, coo.numpy(), vals.numpy(), F
 
 
-@pytest.mark.parametrize("variant", [0, 2])
+@pytest.mark.parametrize("variant", [0, 2, 3])
 def test_wait_runs_out_reports_timeout_and_context_survives(variant):
     dims, R, c, v, F = _tensor()
     Fd = [f.cuda() for f in F]
