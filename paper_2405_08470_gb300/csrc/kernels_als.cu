@@ -15,6 +15,7 @@
 
 #include "engine.h"
 #include "als.h"
+#include "mttkrp_common.cuh"  // paired FP32 arithmetic (fma2)
 
 namespace spm {
 
@@ -146,11 +147,15 @@ __global__ void __launch_bounds__(256) gram_tile_kernel(const T* __restrict__ A,
       for (int rr = g; rr < RT; rr += NG) {
         const float4 x = *reinterpret_cast<const float4*>(&sm[rr * LD + r0]);
         const float4 y = *reinterpret_cast<const float4*>(&sm[rr * LD + c0]);
-        const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+        const float2 y01 = make_float2(y.x, y.y), y23 = make_float2(y.z, y.w);
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xv[a], yv[b], acc[a][b]);
+        for (int a = 0; a < 4; ++a) {  // paired FMAs: the same result as four fmaf
+          float2* a2 = reinterpret_cast<float2*>(acc[a]);
+          const float2 xa = make_float2(xv[a], xv[a]);
+          a2[0] = fma2(xa, y01, a2[0]);
+          a2[1] = fma2(xa, y23, a2[1]);
+        }
       }
     }
   }
@@ -377,12 +382,14 @@ __global__ void __launch_bounds__(256) als_rows_kernel(const float* __restrict__
 #pragma unroll 8
     for (int j = 0; j < RP; ++j) {
       const float4 v = *reinterpret_cast<const float4*>(&Vs[j * RP + c0]);
-      const float vv[4] = {v.x, v.y, v.z, v.w};
+      const float2 v01 = make_float2(v.x, v.y), v23 = make_float2(v.z, v.w);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 4; ++k) {  // paired FMAs: the same result as four fmaf
         const float m = Ms[(rs + RS * k) * LD + j];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) u[k][b] = fmaf(m, vv[b], u[k][b]);
+        const float2 mm = make_float2(m, m);
+        float2* u2 = reinterpret_cast<float2*>(u[k]);
+        u2[0] = fma2(mm, v01, u2[0]);
+        u2[1] = fma2(mm, v23, u2[1]);
       }
     }
 #pragma unroll
