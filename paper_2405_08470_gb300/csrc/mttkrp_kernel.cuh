@@ -514,6 +514,7 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
     }
     typename Landing<T, VW, RC>::type raw[U][NI];
     typename Landing<T, VW, RC>::type rown[LOSS ? U : 1];  // A_n[i_n] slices (fused loss)
+    float hh[LOSS ? U : 1][NV];  // fused loss: the product of the two gathered slices
     if constexpr (LOSS) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -557,7 +558,10 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
           Landing<T, VW, RC>::unpack(raw[u][1], x);
           Landing<T, VW, RC>::unpack(rown[u], y);
 #pragma unroll
-          for (int q = 0; q < NV; ++q) m[u] = fmaf(p[q] * x[q], y[q], m[u]);
+          for (int q = 0; q < NV; ++q) {
+            hh[u][q] = p[q] * x[q];  // kept: the gradient's product below
+            m[u] = fmaf(hh[u][q], y[q], m[u]);
+          }
           if (!lane_live) m[u] = 0.f;
         }
       }
@@ -601,16 +605,23 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
       for (int u = 0; u < U; ++u) {
         if (u < nb) {
           float prod[NV], x[NV];
-          Landing<T, VW, RC>::unpack(raw[u][0], prod);
+          if constexpr (LOSS) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q) prod[q] = hh[u][q];
+          } else {
+            Landing<T, VW, RC>::unpack(raw[u][0], prod);
+          }
           if constexpr (NV % 2 == 0) {  // paired FP32: half the instructions
             float2* p2 = reinterpret_cast<float2*>(prod);
+            if constexpr (!LOSS) {
 #pragma unroll
-            for (int j = 1; j < NI; ++j) {
-              if (j < N - 1) {
-                Landing<T, VW, RC>::unpack(raw[u][j], x);
-                const float2* x2 = reinterpret_cast<const float2*>(x);
+              for (int j = 1; j < NI; ++j) {
+                if (j < N - 1) {
+                  Landing<T, VW, RC>::unpack(raw[u][j], x);
+                  const float2* x2 = reinterpret_cast<const float2*>(x);
 #pragma unroll
-                for (int q = 0; q < NV / 2; ++q) p2[q] = mul2(p2[q], x2[q]);
+                  for (int q = 0; q < NV / 2; ++q) p2[q] = mul2(p2[q], x2[q]);
+                }
               }
             }
             float2* a2 = reinterpret_cast<float2*>(acc);
@@ -618,12 +629,14 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
 #pragma unroll
             for (int q = 0; q < NV / 2; ++q) a2[q] = fma2(p2[q], vv, a2[q]);
           } else {
+            if constexpr (!LOSS) {
 #pragma unroll
-            for (int j = 1; j < NI; ++j) {
-              if (j < N - 1) {
-                Landing<T, VW, RC>::unpack(raw[u][j], x);
+              for (int j = 1; j < NI; ++j) {
+                if (j < N - 1) {
+                  Landing<T, VW, RC>::unpack(raw[u][j], x);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) prod[q] *= x[q];
+                  for (int q = 0; q < NV; ++q) prod[q] *= x[q];
+                }
               }
             }
 #pragma unroll
@@ -637,13 +650,18 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
     for (int u = 0; u < U; ++u) {
       if (u < nb) {
         float prod[NV], x[NV];
-        Landing<T, VW, RC>::unpack(raw[u][0], prod);
+        if constexpr (LOSS) {
 #pragma unroll
-        for (int j = 1; j < NI; ++j) {
-          if (j < N - 1) {
-            Landing<T, VW, RC>::unpack(raw[u][j], x);
+          for (int q = 0; q < NV; ++q) prod[q] = hh[u][q];
+        } else {
+          Landing<T, VW, RC>::unpack(raw[u][0], prod);
 #pragma unroll
-            for (int q = 0; q < NV; ++q) prod[q] *= x[q];
+          for (int j = 1; j < NI; ++j) {
+            if (j < N - 1) {
+              Landing<T, VW, RC>::unpack(raw[u][j], x);
+#pragma unroll
+              for (int q = 0; q < NV; ++q) prod[q] *= x[q];
+            }
           }
         }
         if (rows[u] != cur) {
