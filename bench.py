@@ -642,7 +642,8 @@ def c4_als(args, stream, reps):
     Gram Hadamard and Cholesky on the GPU, the solve and the column scaling,
     replayed as one CUDA graph) on the 5-mode 60M and 6-mode 40M tensors at
     R = 16, 32, 64, each plan autotuned; host-timed per iteration including the
-    read-back of the fit (median of 5 after the capture)."""
+    read-back of the fit (median of 5 after the capture); and the ALS loop as one
+    graph launch (cp_als_run, five iterations), host-timed per iteration."""
     from paper_2405_08470_gb300 import Plan
     out = {}
     for name, ci in (("c4a", 3), ("c4b", 3)):
@@ -669,9 +670,17 @@ def c4_als(args, stream, reps):
                 t0 = time.perf_counter()
                 fits.append(p.als_iter(F, lam))
                 ts.append((time.perf_counter() - t0) * 1e3)
+            # the ALS loop as one graph launch (column scales folded; 5 iterations,
+            # tol 0): the first call captures it, the second is timed
+            p.als_run(F, lam, 5, 0.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            run_fits = p.als_run(F, lam, 5, 0.0)
+            t_run = (time.perf_counter() - t0) / len(run_fits) * 1e3
             ent[f"R{R}"] = {"als_iter_ms": float(np.median(ts)), "sweep_ms": sweep_ms,
                             "fits": fits, "nblk": p.info()["nblk"],
-                            "kernel_form": p.info()["variant"]}
+                            "kernel_form": p.info()["variant"],
+                            "loop_graph_ms_per_iter": t_run, "loop_last_fit": run_fits[-1]}
             p.close()
             del F
             torch.cuda.empty_cache()

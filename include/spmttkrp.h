@@ -224,13 +224,18 @@ int spmttkrp_sweep(spmttkrp_plan_t plan, const void* const* factors, float* cons
 int cp_als_iter(spmttkrp_plan_t plan, void* const* factors, float* lambda, double* fit);
 
 /*
- * Up to max_iters CP-ALS iterations (each as cp_als_iter) run as ONE graph
- * launch, stopping on the device once the fit changes by less than tol between
- * two iterations (the convergence check of the ALS loop, Section 2.1.4): a chain
- * of conditional graph nodes, each holding one iteration and its check, which
- * decides whether the next node runs.  No host synchronisation happens between
- * iterations; the call synchronizes once at the end.  The graph is built on
- * the first call and replayed by later calls with the same pointers,
+ * Up to max_iters CP-ALS iterations run as ONE graph launch, stopping on the
+ * device once the fit changes by less than tol between two iterations (the
+ * convergence check of the ALS loop, Section 2.1.4): a chain of conditional
+ * graph nodes, each holding one iteration and its check, which decides whether
+ * the next node runs.  Column scales are folded: inside the loop each
+ * U_n = M_n V^-1 is stored unnormalised (the mode update followed by the
+ * normalisation does not depend on the other factors' column scales), the fit is
+ * that of the stored factors' model, and after the last iteration every factor
+ * is divided by its column 2-norms and lambda_r = prod_k |U_k[:, r]|.  The
+ * results are cp_als_iter's up to rounding.  No host synchronisation happens
+ * between iterations; the call synchronizes once at the end.  The graph is built
+ * on the first call and replayed by later calls with the same pointers,
  * max_iters, tol and working-copy buffer.
  *   factors   host array of nmodes device pointers, read and overwritten.
  *   lambda    device, float [rank], written.

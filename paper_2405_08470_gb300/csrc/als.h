@@ -22,6 +22,12 @@ int launch_als_lambda(const double* colsq, int nb, int R, double* lam64, float* 
 int launch_als_scale(const float* U, const float* M, const float* vinv, void* A, int dtype,
                      const double* lam64, int64_t I, int R, double* mdot, const int* status,
                      int nb, cudaStream_t s);
+int launch_fill_f64(double* p, int n, double v, cudaStream_t s);
+// The end of a column-scale-folded loop: lambda_r = prod_k sqrt(G_k[r, r]) and
+// every factor divided by its column norms (the Grams must be the stored factors').
+int launch_als_fold_finish(void* const* factors, int dtype, const int64_t* dims, int N, int R,
+                           const double* grams, double* lam64, float* lam_out, const int* status,
+                           int nb, cudaStream_t s);
 int launch_als_fit(const double* grams, int N, int R, const double* lam64, const double* mdot,
                    int nb, double normx2, double* fit_out, const int* status, cudaStream_t s);
 int launch_cp_fwd(const uint8_t* elems, uint8_t* res, int64_t nnz, int es, int N,

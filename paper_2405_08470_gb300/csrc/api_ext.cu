@@ -45,7 +45,10 @@ static int ensure_als(spmttkrp_plan* p) {
   if ((st = ensure(p, (void**)&p->d_red, (size_t)2 * p->red_nb * R * 8))) return st;
   if ((st = ensure(p, (void**)&p->d_chol, 2 * R * R * 8))) return st;
   if ((st = ensure(p, (void**)&p->d_vinv, R * R * 4))) return st;
-  if ((st = ensure(p, (void**)&p->d_scal, (8 + R) * 8))) return st;
+  if (!p->d_scal) {  // [8, 8 + R): lambda; [8 + R, 8 + 2R): ones (the folded loop's lambda)
+    if ((st = plan_dalloc(p, (void**)&p->d_scal, (8 + 2 * R) * 8))) return st;
+    if ((st = launch_fill_f64(p->d_scal + 8 + R, (int)R, 1.0, p->stream))) return st;
+  }
   if (!p->als_side) SPM_CUDA(cudaStreamCreateWithFlags(&p->als_side, cudaStreamNonBlocking));
   if (!p->als_fork) SPM_CUDA(cudaEventCreateWithFlags(&p->als_fork, cudaEventDisableTiming));
   if (!p->als_join) SPM_CUDA(cudaEventCreateWithFlags(&p->als_join, cudaEventDisableTiming));
@@ -59,12 +62,17 @@ static int ensure_als(spmttkrp_plan* p) {
 // into p->stream; under stream capture they become a parallel branch).
 // grams_current: the plan's Grams already belong to these factors (the previous
 // iteration of the same loop formed them), so none is formed first.
+// fold: column-scale folding (cp_als_run): each U_n = M_n V^-1 is stored as it
+// is, with no column norms, lambda or normalisation; the fit is that of the model
+// of the stored factors (lambda = 1), the same model; the loop normalises at its
+// end (launch_als_fold_finish).
 static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda,
-                       bool grams_current = false) {
+                       bool grams_current = false, bool fold = false) {
   const int N = p->N, R = p->R;
   int* status = reinterpret_cast<int*>(p->d_scal);
   double* fit = p->d_scal + 1;
   double* lam64 = p->d_scal + 8;
+  const double* lam_one = p->d_scal + 8 + R;
   double* colsq = p->d_red;
   double* mdot = p->d_red + (size_t)p->red_nb * R;
   cudaStream_t s = p->stream, side = p->als_side;
@@ -84,11 +92,15 @@ static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda,
     const int64_t I = p->dims[(size_t)n];
     if ((st = compute_mode(p, n, cf.data(), p->d_M, false))) return st;
     SPM_CUDA(cudaStreamWaitEvent(s, p->als_join, 0));  // V^-1 of mode n is ready
-    if ((st = launch_als_solve(p->d_M, p->d_U, p->d_vinv, I, R, colsq, status, p->red_nb, s)))
+    if (!fold || R > 64) {  // the column norms (R > 64: U itself, for the scale pass)
+      if ((st = launch_als_solve(p->d_M, p->d_U, p->d_vinv, I, R, colsq, status, p->red_nb, s)))
+        return st;
+    }
+    if (!fold && (st = launch_als_lambda(colsq, p->red_nb, R, lam64, lambda, status, s)))
       return st;
-    if ((st = launch_als_lambda(colsq, p->red_nb, R, lam64, lambda, status, s))) return st;
-    if ((st = launch_als_scale(p->d_U, p->d_M, p->d_vinv, factors[n], p->dtype, lam64, I, R,
-                               mdot, status, p->red_nb, s)))
+    // A_n = U / lambda, or with folding U / 1 = U itself; and <M, A_n>
+    if ((st = launch_als_scale(p->d_U, p->d_M, p->d_vinv, factors[n], p->dtype,
+                               fold ? lam_one : lam64, I, R, mdot, status, p->red_nb, s)))
       return st;
     // side: the updated factor's Gram, then the next mode's Cholesky
     SPM_CUDA(cudaEventRecord(p->als_fork, s));
@@ -102,7 +114,8 @@ static int als_enqueue(spmttkrp_plan* p, void* const* factors, float* lambda,
     SPM_CUDA(cudaEventRecord(p->als_join, side));
   }
   SPM_CUDA(cudaStreamWaitEvent(s, p->als_join, 0));
-  return launch_als_fit(p->d_gram, N, R, lam64, mdot, p->red_nb, p->normx2, fit, status, s);
+  return launch_als_fit(p->d_gram, N, R, fold ? lam_one : lam64, mdot, p->red_nb, p->normx2, fit,
+                        status, s);
 }
 
 static void drop_graphs(std::vector<GraphCache>& v) {
@@ -335,7 +348,7 @@ int cp_als_run(spmttkrp_plan_t p, void* const* factors, float* lambda, int max_i
       e = cudaStreamBeginCaptureToGraph(p->stream, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        st = als_enqueue(p, factors, lambda, t > 0);  // iteration t-1 formed the Grams
+        st = als_enqueue(p, factors, lambda, t > 0, true);  // iteration t-1 formed the Grams
         if (!st)
           st = launch_als_converge(p->d_scal + 1, status, p->d_fits, d_iters, t, tol,
                                    t + 1 < max_iters ? h[(size_t)t + 1] : h[(size_t)t],
@@ -346,6 +359,20 @@ int cp_als_run(spmttkrp_plan_t p, void* const* factors, float* lambda, int max_i
       }
       p->stream = user;
       prev = node;
+    }
+    // after the last iteration that ran: the folded column scales become lambda
+    if (e == cudaSuccess && !st) {
+      p->stream = p->cap_stream;
+      e = cudaStreamBeginCaptureToGraph(p->stream, g, &prev, nullptr, 1,
+                                        cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        st = launch_als_fold_finish(factors, p->dtype, p->dims.data(), p->N, p->R, p->d_gram,
+                                    p->d_scal + 8, lambda, status, p->red_nb, p->stream);
+        cudaGraph_t cap = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(p->stream, &cap);
+        if (e == cudaSuccess) e = e2;
+      }
+      p->stream = user;
     }
     p->stream = user;
     p->cur_buf = buf0;

@@ -446,6 +446,46 @@ __global__ void als_lambda_kernel(const double* __restrict__ colsq_part, int nb,
   }
 }
 
+// ---- Column-scale folding (cp_als_run).  The mode-n update followed by the
+// 2-norm normalisation does not depend on the column scales of the other
+// factors: scaling column r of A_k (k != n) by c scales column r of M_n by c and
+// row and column r of V by c, so M_n V^-1 changes by 1/c in column r, which the
+// normalisation removes.  The loop therefore stores U_n = M_n V^-1 as it is,
+// with its Gram taken from the stored factor, and normalises once after the
+// last iteration: A_k = U_k / |U_k[:, r]| with the norms read off the diagonals
+// of the Grams, lambda_r = prod_k |U_k[:, r]|, the weight of rank-one term r of
+// the same model.
+__global__ void fill_f64_kernel(double* __restrict__ p, int n, double v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+__global__ void als_fold_lambda_kernel(const double* __restrict__ grams, int N, int R,
+                                       double* __restrict__ lam64, float* __restrict__ lam_out,
+                                       const int* __restrict__ status) {
+  if (*status) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double l = 1.0;
+  for (int k = 0; k < N; ++k) l *= sqrt(grams[(size_t)k * R * R + (size_t)r * R + r]);
+  lam64[r] = l;
+  lam_out[r] = (float)l;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) als_normalize_kernel(T* __restrict__ A, int64_t I, int R,
+                                                            const double* __restrict__ gram,
+                                                            const int* __restrict__ status) {
+  __shared__ float inv[256];
+  if (*status) return;
+  for (int r = threadIdx.x; r < R; r += 256)
+    inv[r] = (float)(1.0 / sqrt(gram[(size_t)r * R + r]));
+  __syncthreads();
+  const int64_t n = I * R;
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)gridDim.x * 256)
+    A[e] = from_f<T>(to_f<T>(A[e]) * inv[(int)(e % R)]);
+}
+
 // ---- A_n = U / lambda (stored as T); per-block sums of M * A_n (for <X, Y>)
 template <typename T, int CC>
 __global__ void __launch_bounds__(256) als_scale_kernel(const float* __restrict__ U,
@@ -674,6 +714,30 @@ int launch_als_scale(const float* U, const float* M, const float* vinv, void* A,
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SPM_OK : cuda_fail(e, "als_scale_kernel");
+}
+
+int launch_fill_f64(double* p, int n, double v, cudaStream_t s) {
+  fill_f64_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, n, v);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "fill_f64_kernel");
+}
+
+int launch_als_fold_finish(void* const* factors, int dtype, const int64_t* dims, int N, int R,
+                           const double* grams, double* lam64, float* lam_out, const int* status,
+                           int nb, cudaStream_t s) {
+  if (R > 256) return fail(SPM_ERR_UNSUPPORTED, "rank above 256");
+  als_fold_lambda_kernel<<<(R + 127) / 128, 128, 0, s>>>(grams, N, R, lam64, lam_out, status);
+  for (int k = 0; k < N; ++k) {
+    const double* G = grams + (size_t)k * R * R;
+    if (dtype == SPM_DTYPE_BF16)
+      als_normalize_kernel<__nv_bfloat16><<<nb, 256, 0, s>>>(
+          static_cast<__nv_bfloat16*>(factors[k]), dims[k], R, G, status);
+    else
+      als_normalize_kernel<float><<<nb, 256, 0, s>>>(static_cast<float*>(factors[k]), dims[k], R,
+                                                     G, status);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SPM_OK : cuda_fail(e, "ALS normalisation kernels");
 }
 
 int launch_als_fit(const double* grams, int N, int R, const double* lam64, const double* mdot,
