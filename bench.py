@@ -390,7 +390,8 @@ def extra_measurements(args, plan, spec, coo_h, vals_h, F, outs, R, fseed, strea
     ms32 = time_events(lambda: loss_step(plan, Fg), reps, stream)
     res["cp_loss_fwd_bwd"] = {"f32": {"nnz_per_s": nnz / (ms32 * 1e-3), "ms": ms32}}
     # BF16 factors: sweep time and CP loss on a BF16 plan of the same tensor
-    pb = Plan(coo_h, vals_h, spec.dims, R, dtype="bf16", nblk=args.nblk, tile=args.tile)
+    pb = Plan(coo_h, vals_h, spec.dims, R, dtype="bf16", nblk=args.nblk, tile=args.tile,
+              element_bytes=args.element_bytes)
     Fb = [f.to(torch.bfloat16) for f in F]
     ob = [torch.empty_like(o) for o in outs]
     if args.autotune:

@@ -261,8 +261,8 @@ enum { SPM_LOSS_FORWARD_ONLY = 1 /* no gradient will follow: the plain forward p
 
 /*
  * cp_loss_fwd with flags.  By default (flags 0) a plan whose nonzeros are
- * 3-mode 32-byte sectors (and whose factors are 16-byte aligned, R a multiple
- * of 4) runs one fused pass in the working copy's current mode n: it computes
+ * 3-mode, 16 or 32 bytes (and whose factors are 16-byte aligned, R a multiple
+ * of 4), split contiguously, runs one fused pass in the working copy's current mode n: it computes
  * the residuals, the loss, the gradient dL/dA_n (kept in the plan until the
  * next cp_loss_bwd scales it by grad_out), and writes the residual copy
  * directly in the mode-(n+1) order, so the backward needs N-1 passes instead

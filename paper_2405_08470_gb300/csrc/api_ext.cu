@@ -268,10 +268,11 @@ int cp_als_iter(spmttkrp_plan_t p, void* const* factors, float* lambda, double* 
   return SPM_OK;
 }
 
-// The fused CP-loss pass serves plans whose nonzeros are 3-mode 32-byte sectors
+// The fused CP-loss pass serves plans whose nonzeros are 3-mode, 16 or 32 bytes,
 // and whose factors take the vector lanes (16-byte aligned, R a multiple of 4).
 static bool loss_fusable(const spmttkrp_plan* p, const void* const* factors) {
-  if (!(p->N == 3 && p->es == 32 && p->partition == 0 && p->nnz > 0)) return false;
+  if (!(p->N == 3 && (p->es == 32 || p->es == 16) && p->partition == 0 && p->nnz > 0))
+    return false;
   bool al = true;
   for (int k = 0; k < p->N; ++k) al = al && (((uintptr_t)factors[k] & 15u) == 0);
   return lane_config(p->R, p->dtype, al, true).vec;

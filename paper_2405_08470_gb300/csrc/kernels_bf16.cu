@@ -26,9 +26,24 @@ static int launch_direct_bfloat16(const MttkrpArgs& a, const LaneCfg& c, cudaStr
 }
 
 int launch_mttkrp_bf16(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
-  if (a.loss_part) {  // fused CP-loss pass (3 modes, 32-byte nonzeros, vector lanes)
-    if (!(c.vec && a.nmodes == 3 && a.es == 32))
-      return fail(SPM_ERR_UNSUPPORTED, "fused CP-loss pass: 3 modes, 32-byte nonzeros only");
+  if (a.loss_part) {  // fused CP-loss pass (3 modes, 16- or 32-byte nonzeros, vector lanes)
+    if (!(c.vec && a.nmodes == 3 && (a.es == 32 || a.es == 16)))
+      return fail(SPM_ERR_UNSUPPORTED,
+                  "fused CP-loss pass: 3 modes, 16- or 32-byte nonzeros only");
+    if (a.es == 16) {
+      if (c.VW == 4) {
+        switch (a.mode) {
+          case 0: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 4, 0, 16, true>(a, c.L, s);
+          case 1: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 4, 1, 16, true>(a, c.L, s);
+          default: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 4, 2, 16, true>(a, c.L, s);
+        }
+      }
+      switch (a.mode) {
+        case 0: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 0, 16, true>(a, c.L, s);
+        case 1: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 1, 16, true>(a, c.L, s);
+        default: return launch_warp_kernel<3, __nv_bfloat16, 8, 1, 4, 2, 16, true>(a, c.L, s);
+      }
+    }
     if (c.VW == 4) {
       switch (a.mode) {
         case 0: return launch_warp_kernel<3, __nv_bfloat16, 4, 1, 4, 0, 32, true>(a, c.L, s);

@@ -25,9 +25,17 @@ static int launch_direct_float(const MttkrpArgs& a, const LaneCfg& c, cudaStream
 }
 
 int launch_mttkrp_f32(const MttkrpArgs& a, const LaneCfg& c, cudaStream_t s) {
-  if (a.loss_part) {  // fused CP-loss pass (3 modes, 32-byte nonzeros, vector lanes)
-    if (!(c.vec && a.nmodes == 3 && a.es == 32))
-      return fail(SPM_ERR_UNSUPPORTED, "fused CP-loss pass: 3 modes, 32-byte nonzeros only");
+  if (a.loss_part) {  // fused CP-loss pass (3 modes, 16- or 32-byte nonzeros, vector lanes)
+    if (!(c.vec && a.nmodes == 3 && (a.es == 32 || a.es == 16)))
+      return fail(SPM_ERR_UNSUPPORTED,
+                  "fused CP-loss pass: 3 modes, 16- or 32-byte nonzeros only");
+    if (a.es == 16) {
+      switch (a.mode) {
+        case 0: return launch_warp_kernel<3, float, 4, 1, 4, 0, 16, true>(a, c.L, s);
+        case 1: return launch_warp_kernel<3, float, 4, 1, 4, 1, 16, true>(a, c.L, s);
+        default: return launch_warp_kernel<3, float, 4, 1, 4, 2, 16, true>(a, c.L, s);
+      }
+    }
     switch (a.mode) {
       case 0: return launch_warp_kernel<3, float, 4, 1, 4, 0, 32, true>(a, c.L, s);
       case 1: return launch_warp_kernel<3, float, 4, 1, 4, 1, 32, true>(a, c.L, s);

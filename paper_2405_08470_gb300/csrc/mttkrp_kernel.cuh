@@ -161,7 +161,7 @@ struct Landing<T, 1, RC> {
 // U: nonzeros in flight per lane group; MODE: output mode at compile time (3
 // modes only; -1 = runtime); ESB: element bytes when fixed (0 = the smallest
 // multiple of 16 that holds N indices and the value).
-// LOSS (3 modes, 32-byte nonzeros): the fused first pass of the CP loss.  Each
+// LOSS (3 modes, 16- or 32-byte nonzeros): the fused first pass of the CP loss.  Each
 // nonzero's own factor row A_n[i_n] is gathered as well; the model value
 // m_e = sum_r prod_k A_k[i_k, r] and the residual e = m_e - x_e replace the
 // value in the pass (so `out` receives the mode-n gradient of L = 1/2 sum e^2),
@@ -293,8 +293,8 @@ template <int NT, typename T, int VW, int RC, int U, int MODE, int ESB = 0, bool
           bool RWARP = false>
 __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LOSS) ? 3 : 2))
     mttkrp_warp_kernel(const MttkrpArgs a, const int L) {
-  static_assert(!LOSS || (NT == 3 && MODE >= 0 && VW > 1 && ESB == 32),
-                "the fused CP-loss pass is built for 3 modes and 32-byte nonzeros");
+  static_assert(!LOSS || (NT == 3 && MODE >= 0 && VW > 1 && (ESB == 32 || ESB == 16)),
+                "the fused CP-loss pass is built for 3 modes and 16- or 32-byte nonzeros");
   static_assert(!RWARP || (NT == 3 && MODE >= 0 && VW > 1 && ESB == 32 && !LOSS),
                 "the remap warp is built for 3 modes and 32-byte nonzeros");
   constexpr int CW = RWARP ? kWarps - 1 : kWarps;  // warps that compute

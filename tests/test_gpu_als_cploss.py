@@ -221,12 +221,14 @@ def test_autotune_keeps_results_and_caches(tmp_path, monkeypatch):
     p2.close()
 
 
+@pytest.mark.parametrize("eb", [0, 16])
 @pytest.mark.parametrize("dtype,R", [("f32", 32), ("bf16", 32), ("f32", 64), ("bf16", 16)])
-def test_fused_and_plain_forward_give_the_same_loss_and_gradients(dtype, R):
+def test_fused_and_plain_forward_give_the_same_loss_and_gradients(dtype, R, eb):
     """The fused forward (residuals, the current mode's gradient and the residual
     copy in the next order, in one pass) against the plain forward followed by a
     full backward sweep: equal loss and gradients within FP32 summation order,
-    both against the FP64 oracle, and the working copy untouched by either."""
+    both against the FP64 oracle, and the working copy untouched by either; for
+    32-byte (default) and unpadded 16-byte nonzeros."""
     dims = (300, 200, 120)
     coo, _ = synth.make_coo(dims, 40_000, (1.1, 1.1, 1.1), seed=R + 5)
     x = synth.make_planted_targets(coo, dims, 8, 0.1, seed=6)
@@ -235,7 +237,8 @@ def test_fused_and_plain_forward_give_the_same_loss_and_gradients(dtype, R):
     tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
     Fd = [f.to(tdt).cuda() for f in F]
     Fq = [f.to(tdt).float().numpy().astype(np.float64) for f in F]
-    p = Plan(c, xv, dims, R, dtype=dtype, nblk=57)
+    p = Plan(c, xv, dims, R, dtype=dtype, nblk=57, element_bytes=eb)
+    assert p.info()["elem_bytes"] == (eb or 32)
     want_loss, _ = O.cp_loss(c, xv, Fq)
     G = O.cp_loss_grad(c, xv, dims, Fq)
     idx0, _ = p.elements()
