@@ -535,46 +535,55 @@ def memory_ceiling(nnz, stream, reps):
 
 
 def c3_precision(args, stream, reps):
-    """Configuration 3: 4-mode 1000000x20000x2000x500, 150M nonzeros, R=32: one
-    all-mode sweep with FP32 and with BF16 factors (autotuned), each with its
+    """Configuration 3: 4-mode 1000000x20000x2000x500, 150M nonzeros, R=32 and 64:
+    one all-mode sweep with FP32 and with BF16 factors (autotuned), each with its
     per-mode normwise error against the FP64 oracle on sampled output rows (BF16:
     against the oracle on the BF16-rounded factors, the accumulation error, and
-    on the FP32 factors, the quantisation error)."""
+    on the FP32 factors, the quantisation error).  R=32 at the top level, R=64
+    under "R64"."""
     import oracle as O
     from paper_2405_08470_gb300 import Plan
     spec = synth.workload("c3")
-    R = 32
     coo, vals = synth.make_coo(spec.dims, spec.nnz, spec.skew, spec.seed, device="cuda")
     coo_h, vals_h = coo.cpu().numpy(), vals.cpu().numpy()
     del coo, vals
     torch.cuda.empty_cache()
-    F = synth.make_factors(spec.dims, R, seed=synth.factor_seed(2), device="cuda")
-    F64 = [f.double().cpu().numpy() for f in F]
-    Fq64 = [f.to(torch.bfloat16).double().cpu().numpy() for f in F]
     rows = [_sample_rows(d, 24, 30 + n) for n, d in enumerate(spec.dims)]
-    want = [O.mttkrp_rows(coo_h, vals_h, F64, n, rows[n]) for n in range(4)]
-    wantq = [O.mttkrp_rows(coo_h, vals_h, Fq64, n, rows[n]) for n in range(4)]
-    out = {"workload": spec.name, "rank": R, "nnz": spec.nnz,
-           "rows_checked_per_mode": [len(r) for r in rows]}
-    for dt in ("f32", "bf16"):
-        Fd = [f.to(torch.bfloat16) for f in F] if dt == "bf16" else F
-        p = Plan(coo_h, vals_h, spec.dims, R, dtype=dt)
-        outs = [torch.empty(d, R, device="cuda") for d in spec.dims]
-        p.autotune(Fd, outs)
-        ms = time_events(lambda: p.sweep(Fd, outs, graph=True), reps, stream)
-        got = [outs[n].cpu().numpy()[rows[n]].astype(np.float64) for n in range(4)]
-        e = {"ms_per_sweep": ms, "nblk": p.info()["nblk"], "kernel_form": p.info()["variant"]}
-        if dt == "f32":
-            e["err_vs_fp64_per_mode"] = [_rows_err(got[n], want[n]) for n in range(4)]
-        else:
-            e["err_vs_fp64_bf16_factors_per_mode"] = [_rows_err(got[n], wantq[n])
-                                                      for n in range(4)]
-            e["err_vs_fp64_fp32_factors_per_mode"] = [_rows_err(got[n], want[n])
-                                                      for n in range(4)]
-        out[dt] = e
-        p.close()
-        del outs
+
+    def one_rank(R):
+        F = synth.make_factors(spec.dims, R, seed=synth.factor_seed(2), device="cuda")
+        F64 = [f.double().cpu().numpy() for f in F]
+        Fq64 = [f.to(torch.bfloat16).double().cpu().numpy() for f in F]
+        want = [O.mttkrp_rows(coo_h, vals_h, F64, n, rows[n]) for n in range(4)]
+        wantq = [O.mttkrp_rows(coo_h, vals_h, Fq64, n, rows[n]) for n in range(4)]
+        res = {}
+        for dt in ("f32", "bf16"):
+            Fd = [f.to(torch.bfloat16) for f in F] if dt == "bf16" else F
+            p = Plan(coo_h, vals_h, spec.dims, R, dtype=dt)
+            outs = [torch.empty(d, R, device="cuda") for d in spec.dims]
+            p.autotune(Fd, outs)
+            ms = time_events(lambda: p.sweep(Fd, outs, graph=True), reps, stream)
+            got = [outs[n].cpu().numpy()[rows[n]].astype(np.float64) for n in range(4)]
+            e = {"ms_per_sweep": ms, "nblk": p.info()["nblk"], "kernel_form": p.info()["variant"]}
+            if dt == "f32":
+                e["err_vs_fp64_per_mode"] = [_rows_err(got[n], want[n]) for n in range(4)]
+            else:
+                e["err_vs_fp64_bf16_factors_per_mode"] = [_rows_err(got[n], wantq[n])
+                                                          for n in range(4)]
+                e["err_vs_fp64_fp32_factors_per_mode"] = [_rows_err(got[n], want[n])
+                                                          for n in range(4)]
+            res[dt] = e
+            p.close()
+            del outs
+            torch.cuda.empty_cache()
+        del F
         torch.cuda.empty_cache()
+        return res
+
+    out = {"workload": spec.name, "rank": 32, "nnz": spec.nnz,
+           "rows_checked_per_mode": [len(r) for r in rows]}
+    out.update(one_rank(32))
+    out["R64"] = one_rank(64)
     return out
 
 
