@@ -90,6 +90,14 @@ def test_als_not_spd_is_a_status_not_a_fault():
     G = [f.cuda() for f in synth.make_factors(dims, R, seed=9)]
     fit = p.als_iter(G, lam)
     assert np.isfinite(fit)
+    # the ALS loop graph reports the same status and stops at the failing iteration
+    H = [f.cuda() for f in synth.make_factors(dims, R, seed=9)]
+    H[1][:, 2] = 0.0
+    with pytest.raises(SpmError) as ei:
+        p.als_run(H, lam, 4, 0.0)
+    assert ei.value.status == -7
+    fits = p.als_run([f.cuda() for f in synth.make_factors(dims, R, seed=9)], lam, 3, 0.0)
+    assert len(fits) == 3 and all(np.isfinite(fits))
     p.close()
 
 
@@ -308,6 +316,9 @@ def test_als_loop_graph_matches_single_iterations_and_stops_on_the_device(dims, 
     G = [f.cuda() for f in F0]
     two = pa.als_run(G, la, 10, 1.0)
     assert len(two) == 2
+    for k in range(N):  # the normalisation after the loop ran after its early stop too
+        norms = torch.linalg.vector_norm(G[k].double(), dim=0)
+        assert torch.allclose(norms, torch.ones_like(norms), rtol=0, atol=1e-6), k
     # the working copy is still consistent after the loop
     outs = [torch.empty(d, R, device="cuda") for d in dims]
     pa.sweep(G, outs)
