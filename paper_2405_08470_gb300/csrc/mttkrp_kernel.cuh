@@ -289,6 +289,59 @@ __device__ __forceinline__ void remap_warp_tiles(const MttkrpArgs& a, int mode, 
   }
 }
 
+// A lane group's change of output row on the vector path (VW values a lane, VW
+// >= 4): the row that ends (cur, partial sums acc) goes to the group's head slot
+// if it is the run's first row, else straight to M_n after the empty rows before
+// it (and, for the mode's last row, the empty rows after it).  Returns the run's
+// previous row and head flag.  Kept out of line: the batch code, unrolled over its
+// nonzeros, carries one call per nonzero instead of a copy of this.
+template <int VW>
+struct RowAcc {
+  float v[VW];
+};
+template <int VW>
+__device__ __noinline__ int2 close_row(RowAcc<VW> acc, int cur, int prev_in_run, int head,
+                                       float* __restrict__ out, int R, int sub, float sc,
+                                       int last_row, int64_t out_rows, int no_fill, int slot,
+                                       int* __restrict__ srow, int* __restrict__ sprev,
+                                       float* __restrict__ sacc) {
+  const bool live = sub * VW < R;
+  if (head) {
+    if (cur >= 0) {
+      if (sub == 0) {
+        srow[slot] = cur;
+        sprev[slot] = -2;
+      }
+#pragma unroll
+      for (int j = 0; j < VW; ++j)
+        if (sub * VW + j < R) sacc[(size_t)slot * R + sub * VW + j] = acc.v[j];
+      head = 0;
+    }
+  } else {
+    if (!no_fill && live)
+      for (int64_t z = (int64_t)prev_in_run + 1; z < cur; ++z) {
+        float4* d = reinterpret_cast<float4*>(out + z * R + sub * VW);
+#pragma unroll
+        for (int q = 0; q < VW / 4; ++q) d[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    if (live) {
+      float4* d = reinterpret_cast<float4*>(out + (int64_t)cur * R + sub * VW);
+#pragma unroll
+      for (int q = 0; q < VW / 4; ++q)
+        d[q] = make_float4(acc.v[4 * q] * sc, acc.v[4 * q + 1] * sc, acc.v[4 * q + 2] * sc,
+                           acc.v[4 * q + 3] * sc);
+    }
+    if (cur == last_row && !no_fill && live)
+      for (int64_t z = (int64_t)cur + 1; z < out_rows; ++z) {
+        float4* d = reinterpret_cast<float4*>(out + z * R + sub * VW);
+#pragma unroll
+        for (int q = 0; q < VW / 4; ++q) d[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+  }
+  if (cur >= 0) prev_in_run = cur;
+  return make_int2(prev_in_run, head);
+}
+
 template <int NT, typename T, int VW, int RC, int U, int MODE, int ESB = 0, bool LOSS = false,
           bool RWARP = false>
 __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LOSS) ? 3 : 2))
@@ -665,15 +718,26 @@ __global__ void __launch_bounds__(kThreads, ((U <= 4 && VW > 1 && NT <= 3 && !LO
           }
         }
         if (rows[u] != cur) {
-          if (head) {
-            if (cur >= 0) {
-              store_slot(2 * gw, cur, -2, acc);
-              head = false;
-            }
+          if constexpr (VW > 1 && RC == 1 && NT >= 3 && NT <= 5) {  // (6 modes: more spills)
+            RowAcc<NV> ra;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) ra.v[q] = acc[q];
+            const int2 st2 = close_row<NV>(ra, cur, prev_in_run, head ? 1 : 0, out, R, sub, sc,
+                                           a.last_row, out_rows, a.no_fill, 2 * gw, srow, sprev,
+                                           sacc);
+            prev_in_run = st2.x;
+            head = st2.y != 0;
           } else {
-            write_row_group(cur, acc, prev_in_run);
+            if (head) {
+              if (cur >= 0) {
+                store_slot(2 * gw, cur, -2, acc);
+                head = false;
+              }
+            } else {
+              write_row_group(cur, acc, prev_in_run);
+            }
+            if (cur >= 0) prev_in_run = cur;
           }
-          if (cur >= 0) prev_in_run = cur;
           cur = rows[u];
 #pragma unroll
           for (int q = 0; q < NV; ++q) acc[q] = 0.f;
