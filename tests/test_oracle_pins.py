@@ -418,6 +418,41 @@ def test_als_recovers_planted_exact_low_rank_tensor():
     assert fit > 0.999
 
 
+def test_als_update_ignores_the_other_factors_column_scales():
+    """The mode update followed by the 2-norm normalisation (Section 2.1.4's ALS,
+    Kolda-Bader) does not depend on positive column scales of the other factors;
+    lambda absorbs them.  Then a sweep that never normalises inside the loop, and
+    normalises once after it (lambda_r = prod_k |U_k[:, r]|), gives the factors and
+    lambda of the normalised sweeps: the reading the folded ALS loop rests on."""
+    rng = np.random.default_rng(83)
+    coo, vals, dims = tiny_tensor(rng, 3, maxdim=6, density=0.6)
+    R = 3
+    A = [rng.standard_normal((d, R)) for d in dims]
+    for n in range(3):
+        c = [rng.uniform(0.2, 5.0, R) for _ in dims]
+        B = [A[k] * c[k] if k != n else A[k] for k in range(3)]
+        An, la, _ = O.als_mode_update(coo, vals, dims, A, n)
+        Bn, lb, _ = O.als_mode_update(coo, vals, dims, B, n)
+        assert np.allclose(An[n], Bn[n], rtol=0, atol=1e-10)
+        scale = np.prod([c[k] for k in range(3) if k != n], axis=0)
+        assert np.allclose(lb * scale, la, rtol=1e-10, atol=0)
+    # three sweeps: normalised every mode against folded (never normalised inside)
+    F, U = [a.copy() for a in A], [a.copy() for a in A]
+    for it in range(3):
+        F, lam, _ = O.cp_als_iter(coo, vals, dims, F)
+        for n in range(3):
+            M = O.mttkrp(coo, vals, dims, U, n)
+            V = np.ones((R, R))
+            for k in range(3):
+                if k != n:
+                    V = V * (U[k].T @ U[k])
+            U[n] = np.linalg.solve(V, M.T).T
+    norms = [np.linalg.norm(u, axis=0) for u in U]
+    for k in range(3):
+        assert np.allclose(U[k] / norms[k], F[k], rtol=0, atol=1e-8), k
+    assert np.allclose(np.prod(norms, axis=0), lam, rtol=1e-8, atol=0)
+
+
 def test_als_rejects_non_spd():
     coo = np.array([[0, 0, 0], [1, 1, 1]])
     vals = np.array([1.0, 2.0])
