@@ -520,9 +520,9 @@ int spmttkrp_autotune(spmttkrp_plan_t p, const void* const* factors, float* cons
   struct Cand {
     int nps, tile, variant, stages;
   };
-  // blocks per SM: warp blocks (form 0) from 2 to 32 waves of 24 warps (each
-  // block >= 256 nonzeros), tiles whose rings keep two CTAs per SM, 2- or
-  // 3-stage rings; CTA blocks (form 1) in multiples of 4
+  // blocks per SM: warp blocks (form 0) from 48 to 768 (each block >= 256
+  // nonzeros), tiles whose rings keep two CTAs per SM, 2- or 3-stage rings;
+  // CTA blocks (form 1) in multiples of 4
   std::vector<Cand> cands;
   bool default_listed = false;
   for (int n : {48, 96, 192, 384, 768}) default_listed |= n * p->num_sms == nblk_default;
