@@ -162,6 +162,31 @@ def test_null_pointer_and_state_errors():
     p.close()
 
 
+def test_als_and_loss_entry_points_reject_null_and_host_only_plans():
+    """CP-ALS (one iteration and the loop), the CP loss and the autotuner return
+    INVALID_ARG for a null plan and STATE for a host-only plan, before any
+    argument or device is touched."""
+    L = lib()
+    fit = ctypes.c_double()
+    fits = (ctypes.c_double * 4)()
+    iters = ctypes.c_int()
+    calls = {
+        "cp_als_iter": lambda h: L.cp_als_iter(h, None, None, ctypes.byref(fit)),
+        "cp_als_run": lambda h: L.cp_als_run(h, None, None, 4, 0.0, fits, ctypes.byref(iters)),
+        "cp_loss_fwd": lambda h: L.cp_loss_fwd(h, None, None),
+        "cp_loss_fwd_ex": lambda h: L.cp_loss_fwd_ex(h, None, None, 0),
+        "cp_loss_bwd": lambda h: L.cp_loss_bwd(h, None, None, None),
+        "spmttkrp_autotune": lambda h: L.spmttkrp_autotune(h, None, None, 0),
+    }
+    for name, call in calls.items():
+        assert call(None) == -1, name
+    p = _host_plan(np.array([[0, 0, 0], [1, 1, 1]]), np.ones(2, np.float32), (2, 2, 2))
+    for name, call in calls.items():
+        assert call(p._h) == -8, name
+        assert L.spmttkrp_last_error()  # a message for the failed call
+    p.close()
+
+
 def test_check_argument_errors_need_no_device():
     """The consistency check rejects bad arguments before touching the device, and
     refuses host-only plans."""
